@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the PRNGD bulk fill on GB300 (Demchik and Gulov, arXiv:1401.8230, Section 2).
+
+Step = one launch of the hot path over the bulk workload: 2^20 xorshift128 streams (seed 1)
+x 1024 outputs = 2^30 extended-precision uniforms, w = 32, written as correctly rounded
+doubles (form B, integer-only), stream-major, 8 GiB. Per step: the draws, accept-reject,
+n, conversion and the store of every value; the streams continue from step to step, so
+every step produces new numbers. The 8 GiB output exceeds the 129 MB L2, so no flush is
+needed between steps.
+
+Prints ONE JSON line (rank 0). Extra keys measure the other forms, w = 24, the fused
+statistics mode and the end-to-end host path. `--impl reference` times the CPU oracle
+instead (the slow reference arm) on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): each rank fills its own 2^20 streams (rank r takes streams
+[r 2^20, (r+1) 2^20) of the same seed); no data exchange; weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 uniforms Gsamples/s & % HBM-write roofline; batched/served p50/p99 vs plain"
+UNIT = "Gsamples/s"
+SEED = 1
+N_STREAMS = 1 << 20
+PER_STREAM = 1024
+W = 32
+GAMMA = 0x9E3779B97F4A7C15
+PROFILE = os.path.join(ROOT, "profiles", "fill_b32_bulk_2p30.txt")
+KERNEL_SOURCES = ["paper_1401_8230_gb300/csrc/prngd_fill.cuh", "paper_1401_8230_gb300/csrc/prngd_math.cuh"]
+
+
+def workload_desc():
+    return {"workload": "bulk fill: 2^20 xorshift128 streams (seed 1) x 1024 outputs = 2^30 uniforms, "
+                        "w=32, form B (correctly rounded f64, integer-only), stream-major, 8 GiB, one launch",
+            "n_streams": N_STREAMS, "per_stream": PER_STREAM, "w": W, "form": "B", "output": "f64",
+            "l2": "8 GiB output per step > 129 MB L2: no flush"}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_h = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
+    m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_h or not m_t or m_h.group(1) != kernel_hash():
+        return None
+    return float(m_t.group(1))
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        self.dev = device_index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_rate(n_streams_sample: int, first: int = 0, threads: int | None = None):
+    """Oracle form-B fill of streams [first, first + n) x 1024 on all host cores."""
+    import numpy as np
+
+    import oracle as O
+
+    threads = threads or os.cpu_count() or 1
+    chunk = max(1, n_streams_sample // (threads * 4))
+    jobs = [(s, min(chunk, first + n_streams_sample - s)) for s in range(first, first + n_streams_sample, chunk)]
+    O.lib()
+
+    def run(job):
+        s, n = job
+        out = np.empty(n * PER_STREAM, dtype=np.float64)
+        rej = np.empty(n, dtype=np.uint64)
+        rc = O.lib().orc_fill(SEED, s, n, PER_STREAM, W, O.FORM_B, out.ctypes.data, rej.ctypes.data)
+        assert rc == 0
+        return n
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        done = sum(ex.map(run, jobs))
+    dt = time.perf_counter() - t0
+    return done * PER_STREAM / dt / 1e9, dt, threads
+
+
+def cpu_baseline(target_s: float = 10.0):
+    # calibrate on a small sample, then time a sample sized for ~target_s of wall time
+    rate, _, threads = oracle_rate(256)
+    n = int(max(256, min(N_STREAMS, rate * 1e9 * target_s / PER_STREAM)))
+    rate, dt, threads = oracle_rate(n)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"streams 0..{n - 1} of the bulk workload (seed 1, w=32, form B, 1024 outputs each; "
+                      f"{n * PER_STREAM} samples, {dt:.1f} s wall on {threads} threads)"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    rate, _, threads = oracle_rate(256)
+    n = int(max(256, min(N_STREAMS, rate * 1e9 * 2.0 / PER_STREAM)))  # ~2 s per step
+    for _ in range(args.warmup):
+        oracle_rate(max(64, n // 8))
+    times, total = [], 0
+    for _ in range(args.steps):
+        r, dt, threads = oracle_rate(n)
+        times.append(dt)
+        total += n * PER_STREAM
+    value = total / sum(times) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {**workload_desc(), "sample": f"{n} streams x 1024 per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"streams 0..{n - 1} of the bulk workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def time_calls(torch, fn, reps, stream):
+    """Average device time of fn() over reps launches, CUDA events on `stream`."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_1401_8230_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    # rank r's streams are streams [r n, (r+1) n) of SEED: splitmix64 stream s of seed + 2 r n gamma
+    seed_r = (SEED + 2 * rank * N_STREAMS * GAMMA) % 2**64
+    stream = torch.cuda.current_stream()
+    g = P.Generator(seed_r, N_STREAMS, W)
+    out = torch.empty(N_STREAMS * PER_STREAM, dtype=torch.float64, device="cuda")
+
+    def step():
+        g.fill_f64(out, PER_STREAM, P.FORM_B_INTBITS, None, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start.record(stream)
+    for a, b in evs:
+        a.record(stream)
+        step()
+        b.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    launch_ms = [a.elapsed_time(b) for a, b in evs]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    samples_step = N_STREAMS * PER_STREAM
+    value = world * samples_step * args.steps / (total_ms * 1e-3) / 1e9
+    avg_launch_ms = sum(launch_ms) / len(launch_ms)
+    peak, peak_kind = load_peaks()
+    alg_bytes = samples_step * 8 + N_STREAMS * 32  # outputs written + state read and written
+    achieved = alg_bytes / (avg_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS hbm_gbs)",
+                "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_launch_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {**workload_desc(), "parallelism": f"replicas x{world} (disjoint stream ranges)"},
+            "roofline": roofline, "clocks": clk, "gpu_launches": args.steps}
+
+    if rank == 0 and not args.no_extras:
+        line["forms"] = extras(torch, P, g, out, stream, peak)
+    if rank == 0:
+        line["e2e"] = e2e(torch, P, g, samples_step)
+    del out
+    g.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(torch, P, g, out, stream, peak):
+    """The other forms and modes on the same sizes (average device time of a few launches)."""
+    res = {}
+    n = N_STREAMS * PER_STREAM
+    reps = 10
+
+    def rate(ms):
+        return n / (ms * 1e-3) / 1e9
+
+    for name, fn in [
+        ("w32_formA_fp64", lambda: g.fill_f64(out, PER_STREAM, P.FORM_A_FP64, None, stream)),
+        ("w32_formB_intbits", lambda: g.fill_f64(out, PER_STREAM, P.FORM_B_INTBITS, None, stream)),
+        ("w32_formC_f32pair", lambda: g.fill_f32pair(out, PER_STREAM, None, stream)),
+    ]:
+        fn()
+        ms = sum(time_calls(torch, fn, reps, stream)) / reps
+        res[name] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak}
+    g24 = P.Generator(SEED, N_STREAMS, 24)
+    for name, form in [("w24_formB_intbits", P.FORM_B_INTBITS), ("w24_formA_fp64", P.FORM_A_FP64)]:
+        fn = lambda form=form: g24.fill_f64(out, PER_STREAM, form, None, stream)  # noqa: E731
+        fn()
+        ms = sum(time_calls(torch, fn, reps, stream)) / reps
+        res[name] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak}
+    g24.close()
+    # fused statistics, 2^20 streams x 2^16 = 2^36 samples, no store
+    gs = P.Generator(SEED, N_STREAMS, 32)
+    hist = torch.zeros(65536, dtype=torch.int64, device="cuda")
+    sums = torch.zeros(8, dtype=torch.int64, device="cuda")
+    per = 1 << 16
+    fn = lambda: gs.fused_stats(per, hist, sums, None, stream)  # noqa: E731
+    fn()
+    ms = sum(time_calls(torch, fn, 3, stream)) / 3
+    res["w32_fused_stats_2p36"] = {"gsamples_s": N_STREAMS * per / (ms * 1e-3) / 1e9, "ms": ms}
+    gs.close()
+    return res
+
+
+def e2e(torch, P, g, samples_step):
+    """End to end through the public API: prng_fill_f64_host into pinned host memory (device
+    slices generated and copied back inside the call), one full 2^30-sample step per call."""
+    host = torch.empty(samples_step, dtype=torch.float64, pin_memory=True)
+    g.fill_f64_host(host, PER_STREAM, P.FORM_B_INTBITS)  # warm-up (staging buffers)
+    reps = 3
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.fill_f64_host(host, PER_STREAM, P.FORM_B_INTBITS)
+    dt = (time.perf_counter() - t0) / reps
+    del host
+    return {"value": samples_step / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": samples_step * 8, "ms_per_step": dt * 1e3,
+            "api": "prng_fill_f64_host (pinned host buffer)"}
+
+
+if __name__ == "__main__":
+    sys.exit(main())

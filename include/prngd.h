@@ -1,0 +1,147 @@
+/*
+ * prngd.h -- C ABI of the GB300 PRNGD library (libprngd.so).
+ *
+ * Bulk generation of extended-precision uniform variates by the construction of
+ * V. Demchik and A. Gulov, "Increasing precision of uniform pseudorandom number generators"
+ * (arXiv:1401.8230), Section 2: two w-bit base draws x1, x2 are combined as z = x1 + k x2 with
+ * k = 2^-w (Eq. 1); a pair whose x1 lies on a range end is rejected and the next pair of the
+ * same stream is taken (the discrete accept-reject rule after Fig. 1); the accepted z is
+ * mapped onto the unit interval by Eq. 4, z' = (z - (a0 + k b)) / (a - a0 - k (b - b0)).
+ *
+ * With base draws x1 = a0 + u1 k, x2 = b0 + u2 k (integers u1, u2 in [0, 2^w - 1]) Eq. 4 is
+ * exactly z' = n / D with n = u1 2^w + u2 - (2^w - 1) and D = (2^w - 1)^2, for any offsets
+ * a0, b0; accepted outputs are the D - 1 equally spaced points 1/D .. (D-1)/D.
+ *
+ * Streams: stream s is Marsaglia's xorshift128 seeded from splitmix64 outputs 2s and 2s+1 of
+ * the sequence started at `seed`; a w-bit draw is the top w bits of a 32-bit output. Attempt
+ * j of a stream uses draws 2j (x1) and 2j+1 (x2). Every call continues each stream from its
+ * device-resident state, so a stream's output sequence never depends on launch shapes.
+ *
+ * Conventions for every entry point:
+ *  - Return value: PRNG_OK (0) or one of the PRNG_E* codes below. No exception crosses the ABI.
+ *    prng_last_error() gives a message for the calling thread's most recent failure.
+ *  - "device pointer" means memory the caller allocated on the current CUDA device
+ *    (cudaMalloc, a torch tensor, ...). The caller owns it; the library never frees it.
+ *  - `cuda_stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Device work is enqueued on it and the call returns without synchronising, unless the
+ *    entry point says otherwise.
+ *  - A handle is not thread-safe: calls on one handle must come from one thread at a time,
+ *    and two fills on one handle must not overlap on the GPU (they continue the same state).
+ */
+#ifndef PRNGD_H
+#define PRNGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define PRNG_OK 0
+#define PRNG_EINVAL 1   /* bad argument: null pointer, w out of [2, 32], zero streams,     */
+                        /* ranges that break the step condition, unknown form, ...         */
+#define PRNG_ENOMEM 2   /* a device or pinned-host allocation failed                       */
+#define PRNG_ECUDA 3    /* a CUDA runtime call or kernel launch failed (see prng_last_error) */
+#define PRNG_ETIMEOUT 4 /* a bounded device or host wait gave up                           */
+#define PRNG_EBUSY 5    /* admission refused: the queue or the memory budget is full        */
+#define PRNG_ENOTFOUND 6 /* unknown ticket                                                  */
+
+/* Output forms. All three are functions of the same accepted n; each output is 8 bytes. */
+#define PRNG_FORM_A_FP64 0    /* double RN(RN(n) * C_w), C_w = RN(1/D): the FP64 sequence;  */
+                              /* at most 1 ulp from RN(n/D)                                 */
+#define PRNG_FORM_B_INTBITS 1 /* double RN(n/D), correctly rounded, built with integer ops  */
+#define PRNG_FORM_C_F32PAIR 2 /* two floats (hi, lo): hi = RN32(d), lo = RN32(d - hi), with */
+                              /* d the form-B value; stored interleaved hi, lo               */
+
+typedef struct prng_ctx* prng_t;
+
+/* Human-readable message for the calling thread's last failed call ("" if none). */
+const char* prng_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int prng_version(void);
+
+/*
+ * prng_create -- allocate and seed `n_streams` streams on the current CUDA device.
+ * Section 2 (Eq. 1, Eq. 4): w is the precision of one base draw (2 <= w <= 32) and
+ * [a0, a], [b0, b] are the ranges of x1 and x2. The discrete accept-reject rule assumes both
+ * are grids of step k = 2^-w, so a - a0 and b - b0 must both equal exactly (2^w - 1) 2^-w;
+ * any a0, b0 satisfying this give the same outputs (the offsets cancel in Eq. 4).
+ * Streams 0 .. n_streams-1 of `seed` are seeded on the device; the call synchronises.
+ * Errors: PRNG_EINVAL (out == NULL, n_streams == 0 or > 2^32, w outside [2, 32], ranges with
+ * another step), PRNG_ENOMEM, PRNG_ECUDA. On error *out is set to NULL.
+ */
+int prng_create(prng_t* out, uint64_t seed, uint64_t n_streams, int w, double a0, double a,
+                double b0, double b);
+
+/* Release the handle and its device memory (synchronises the device first). NULL is a no-op. */
+int prng_destroy(prng_t h);
+
+/* Number of streams and w of a handle (either pointer may be NULL). */
+int prng_get_info(prng_t h, uint64_t* n_streams, int* w);
+
+/*
+ * prng_fill_f64 -- per_stream outputs of every stream, as doubles, stream-major:
+ * d_out[s * per_stream + i] is output i of stream s in this call (Algorithm 1 per output;
+ * accept-reject as in Section 2, pair semantics). form is PRNG_FORM_A_FP64 or
+ * PRNG_FORM_B_INTBITS. d_out: device pointer to n_streams * per_stream doubles (8-byte
+ * aligned; 16-byte alignment and an even per_stream select the TMA store path).
+ * d_rejects (nullable): device pointer to n_streams uint64, set to the number of rejected
+ * pairs each stream consumed in this call. per_stream == 0 is a no-op.
+ * Errors: PRNG_EINVAL (null handle or d_out, misaligned d_out, bad form), PRNG_ECUDA.
+ */
+int prng_fill_f64(prng_t h, double* d_out, uint64_t per_stream, int form, uint64_t* d_rejects,
+                  void* cuda_stream);
+
+/*
+ * prng_fill_f32pair -- as prng_fill_f64 with form C: d_out holds 2 * n_streams * per_stream
+ * floats, element 2*(s*per_stream+i) = hi and 2*(s*per_stream+i)+1 = lo of output i of
+ * stream s, with hi = RN32(d), lo = RN32(d - hi) and d = RN(n/D).
+ */
+int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_rejects,
+                      void* cuda_stream);
+
+/*
+ * prng_fill_f64_host -- end-to-end fill into HOST memory: the same values as prng_fill_f64
+ * (the streams advance identically), generated on the device in slices and copied to
+ * `host_out` (n_streams * per_stream doubles, any host memory; pinned memory is fastest),
+ * with generation of the next slice overlapping the copy of the previous one. The call
+ * synchronises. host_rejects (nullable, host memory) receives per-stream reject counts.
+ * Errors: PRNG_EINVAL, PRNG_ENOMEM (staging buffers), PRNG_ECUDA.
+ */
+int prng_fill_f64_host(prng_t h, double* host_out, uint64_t per_stream, int form,
+                       uint64_t* host_rejects);
+
+/*
+ * prng_fused_stats -- generate per_stream outputs of every stream (advancing the streams
+ * exactly as a fill would) and reduce them without storing any value: a 65536-bin
+ * histogram of floor(2^16 z') and the four sums S1 = sum t, S2 = sum p2, S3 = sum p3,
+ * S4 = sum p4 with t = floor(2^32 z'), p2 = floor(t^2 / 2^32), p3 = floor(p2 t / 2^32),
+ * p4 = floor(p3 t / 2^32). z' = n/D exactly (no rounding), so all results are exact
+ * integers independent of summation order; the p-th moment estimate is S_p / (N 2^32).
+ * d_hist: device pointer to 65536 uint64, d_sums: device pointer to 8 uint64 (S_p as a
+ * 128-bit integer, low word at 2(p-1), high word at 2(p-1)+1). Both are ACCUMULATED into
+ * (zero them first for a fresh result). d_rejects as for prng_fill_f64.
+ * Errors: PRNG_EINVAL (null pointers), PRNG_ENOMEM (scratch), PRNG_ECUDA.
+ */
+int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist, uint64_t* d_sums,
+                     uint64_t* d_rejects, void* cuda_stream);
+
+/*
+ * State checkpoint: each stream's state is 16 bytes (xorshift128 words x, y, z, w).
+ * prng_state_bytes gives n_streams * 16. save copies the device state into host_buf and
+ * restore copies it back; both synchronise. A fill after restore reproduces the outputs
+ * that followed the save, bit for bit.
+ * Errors: PRNG_EINVAL (null pointers, bytes != prng_state_bytes), PRNG_ECUDA.
+ */
+size_t prng_state_bytes(prng_t h);
+int prng_state_save(prng_t h, void* host_buf, size_t bytes);
+int prng_state_restore(prng_t h, const void* host_buf, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRNGD_H */

@@ -1,0 +1,191 @@
+"""ctypes declarations of include/prngd.h and argument marshalling (no computation)."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PRNG_OK, PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA, PRNG_ETIMEOUT, PRNG_EBUSY, PRNG_ENOTFOUND = range(7)
+FORM_A_FP64, FORM_B_INTBITS, FORM_C_F32PAIR = 0, 1, 2
+
+_lock = threading.Lock()
+_lib: ctypes.CDLL | None = None
+
+_u64, _i32, _dbl, _vp, _sz = ctypes.c_uint64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+_P = _vp  # opaque handle
+
+# name -> (restype, argtypes); mirrors include/prngd.h
+_SIGNATURES = {
+    "prng_last_error": (ctypes.c_char_p, []),
+    "prng_version": (_i32, []),
+    "prng_create": (_i32, [ctypes.POINTER(_P), _u64, _u64, _i32, _dbl, _dbl, _dbl, _dbl]),
+    "prng_destroy": (_i32, [_P]),
+    "prng_get_info": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(_i32)]),
+    "prng_fill_f64": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
+    "prng_fill_f32pair": (_i32, [_P, _vp, _u64, _vp, _vp]),
+    "prng_fill_f64_host": (_i32, [_P, _vp, _u64, _i32, _vp]),
+    "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
+    "prng_state_bytes": (_sz, [_P]),
+    "prng_state_save": (_i32, [_P, _vp, _sz]),
+    "prng_state_restore": (_i32, [_P, _vp, _sz]),
+}
+
+
+class PrngError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"prngd error {code}: {message}")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libprngd.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != PRNG_OK:
+        raise PrngError(rc, prng_last_error())
+
+
+def _ptr(x) -> int | None:
+    """Device/host address of a tensor-like (data_ptr()), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):  # numpy
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x).__name__}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:  # pragma: no cover
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def prng_last_error() -> str:
+    msg = lib().prng_last_error()
+    return msg.decode() if msg else ""
+
+
+def prng_version() -> int:
+    return int(lib().prng_version())
+
+
+def prng_create(seed: int, n_streams: int, w: int = 32, a0: float = 0.0, a: float | None = None,
+                b0: float = 0.0, b: float | None = None) -> int:
+    step = float((2**w - 1) * 2.0**-w)
+    a = a0 + step if a is None else a
+    b = b0 + step if b is None else b
+    h = _P()
+    _check(lib().prng_create(ctypes.byref(h), seed & (2**64 - 1), n_streams, w, a0, a, b0, b))
+    return h.value
+
+
+def prng_destroy(h: int) -> None:
+    _check(lib().prng_destroy(h))
+
+
+def prng_get_info(h: int) -> tuple[int, int]:
+    n, w = _u64(), _i32()
+    _check(lib().prng_get_info(h, ctypes.byref(n), ctypes.byref(w)))
+    return int(n.value), int(w.value)
+
+
+def prng_fill_f64(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None, stream=None) -> None:
+    _check(lib().prng_fill_f64(h, _ptr(out), per_stream, form, _ptr(rejects), _stream(stream)))
+
+
+def prng_fill_f32pair(h: int, out, per_stream: int, rejects=None, stream=None) -> None:
+    _check(lib().prng_fill_f32pair(h, _ptr(out), per_stream, _ptr(rejects), _stream(stream)))
+
+
+def prng_fill_f64_host(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None) -> None:
+    _check(lib().prng_fill_f64_host(h, _ptr(out), per_stream, form, _ptr(rejects)))
+
+
+def prng_fused_stats(h: int, per_stream: int, hist, sums, rejects=None, stream=None) -> None:
+    _check(lib().prng_fused_stats(h, per_stream, _ptr(hist), _ptr(sums), _ptr(rejects), _stream(stream)))
+
+
+def prng_state_bytes(h: int) -> int:
+    return int(lib().prng_state_bytes(h))
+
+
+def prng_state_save(h: int, buf) -> None:
+    _check(lib().prng_state_save(h, _ptr(buf), prng_state_bytes(h)))
+
+
+def prng_state_restore(h: int, buf) -> None:
+    _check(lib().prng_state_restore(h, _ptr(buf), prng_state_bytes(h)))
+
+
+class Generator:
+    """Owning wrapper of a handle; methods forward to the prng_* functions."""
+
+    def __init__(self, seed: int, n_streams: int, w: int = 32, **ranges):
+        self.h = prng_create(seed, n_streams, w, **ranges)
+        self.n_streams, self.w = prng_get_info(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            prng_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def fill_f64(self, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None, stream=None):
+        prng_fill_f64(self.h, out, per_stream, form, rejects, stream)
+        return out
+
+    def fill_f32pair(self, out, per_stream: int, rejects=None, stream=None):
+        prng_fill_f32pair(self.h, out, per_stream, rejects, stream)
+        return out
+
+    def fill_f64_host(self, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None):
+        prng_fill_f64_host(self.h, out, per_stream, form, rejects)
+        return out
+
+    def fused_stats(self, per_stream: int, hist, sums, rejects=None, stream=None):
+        prng_fused_stats(self.h, per_stream, hist, sums, rejects, stream)
+
+    def state_save(self, buf):
+        prng_state_save(self.h, buf)
+        return buf
+
+    def state_restore(self, buf):
+        prng_state_restore(self.h, buf)

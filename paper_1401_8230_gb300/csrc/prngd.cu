@@ -1,0 +1,277 @@
+// prngd.cu -- host side of the C ABI declared in include/prngd.h: handle management,
+// argument checking, tensor-map encoding and kernel dispatch for the fill paths.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <string>
+
+#include "prngd.h"
+#include "prngd_fill.cuh"
+#include "prngd_internal.h"
+
+using prngd::DivConst;
+using prngd::FillParams;
+
+namespace prngd_host {
+
+thread_local char g_err[512];
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+DivConst make_divconst(int w) {
+  const uint64_t m = (w == 32) ? 0xFFFFFFFFull : ((1ull << w) - 1);
+  const uint64_t D = m * m;
+  DivConst dc;
+  dc.sh = 64 - 2 * w;
+  dc.d_norm = D << dc.sh;
+  const unsigned __int128 all = ~(unsigned __int128)0;
+  dc.v = (uint64_t)(all / dc.d_norm - ((unsigned __int128)1 << 64));
+  return dc;
+}
+
+double scale_constant(const DivConst& dc) {
+  const uint64_t bits = prngd::rn_bits_exact(1, dc);  // RN(1/D)
+  double d;
+  memcpy(&d, &bits, 8);
+  return d;
+}
+
+// ----------------------------------------------------------------- tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 2D map over a stream-major array of 8-byte outputs: dim0 = outputs per stream (contiguous),
+// dim1 = streams; box = 16 outputs x 32 streams with the 128-byte swizzle.
+bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if (((uintptr_t)out & 15) || (per_stream & 1) || per_stream >= (1ull << 31) || n_streams >= (1ull << 31))
+    return false;
+  cuuint64_t gdim[2] = {per_stream, n_streams};
+  cuuint64_t gstride[1] = {per_stream * 8};
+  cuuint32_t box[2] = {(cuuint32_t)prngd::kChunk, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, out, gdim, gstride, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ----------------------------------------------------------------- fill dispatch
+constexpr int kWarpsPerBlock = 8;
+constexpr int kNbuf = 2;
+constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * kNbuf * prngd::kTileBytes + 1024;
+
+template <int W, int FORM>
+static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s) {
+  const uint64_t warps = (p.n_streams + 31) / 32;
+  const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  if (map) {
+    auto k = prngd::fill_tma_kernel<W, FORM, kNbuf>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
+  } else {
+    prngd::fill_plain_kernel<W, FORM><<<blocks, kWarpsPerBlock * 32, 0, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+template <int FORM>
+static cudaError_t launch_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s) {
+  if (p.w == 32) return launch_w_form<32, FORM>(p, map, s);
+  if (p.w == 24) return launch_w_form<24, FORM>(p, map, s);
+  return launch_w_form<0, FORM>(p, map, s);
+}
+
+int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
+                uint64_t* rejects, cudaStream_t s, bool allow_tma) {
+  if (n_streams == 0 || per_stream == 0) return PRNG_OK;
+  FillParams p;
+  p.state = state;
+  p.n_streams = n_streams;
+  p.per_stream = per_stream;
+  p.out = (uint64_t*)out;
+  p.rejects = rejects;
+  p.dc = h->dc;
+  p.scale = h->scale;
+  p.w = h->w;
+  CUtensorMap map;
+  const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
+  cudaError_t e;
+  switch (form) {
+    case PRNG_FORM_A_FP64: e = launch_form<prngd::kFormA>(p, mp, s); break;
+    case PRNG_FORM_B_INTBITS: e = launch_form<prngd::kFormB>(p, mp, s); break;
+    case PRNG_FORM_C_F32PAIR: e = launch_form<prngd::kFormC>(p, mp, s); break;
+    default: return fail(PRNG_EINVAL, "unknown form %d", form);
+  }
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));
+  return PRNG_OK;
+}
+
+int check_handle_device(prng_ctx* h) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev != h->device) return fail(PRNG_EINVAL, "handle lives on device %d, current device is %d", h->device, dev);
+  return PRNG_OK;
+}
+
+}  // namespace prngd_host
+
+using namespace prngd_host;
+
+extern "C" {
+
+const char* prng_last_error(void) { return g_err; }
+
+int prng_version(void) { return 100; }
+
+int prng_create(prng_t* out, uint64_t seed, uint64_t n_streams, int w, double a0, double a, double b0, double b) {
+  g_err[0] = 0;
+  if (!out) return fail(PRNG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (w < 2 || w > 32) return fail(PRNG_EINVAL, "w = %d is outside [2, 32]", w);
+  if (n_streams == 0 || n_streams > (1ull << 32)) return fail(PRNG_EINVAL, "n_streams must be in [1, 2^32]");
+  if (!std::isfinite(a0) || !std::isfinite(a) || !std::isfinite(b0) || !std::isfinite(b))
+    return fail(PRNG_EINVAL, "ranges must be finite");
+  // Discrete rule of Section 2: x1 and x2 are grids of step k = 2^-w with 2^w points each.
+  const double step = std::ldexp((double)((w == 32) ? 0xFFFFFFFFull : ((1ull << w) - 1)), -w);
+  if (a - a0 != step || a0 + step != a || b - b0 != step || b0 + step != b)
+    return fail(PRNG_EINVAL, "ranges must satisfy a - a0 = b - b0 = (2^w - 1) 2^-w exactly");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  prng_ctx* h = new prng_ctx();
+  h->device = dev;
+  h->seed = seed;
+  h->n_streams = n_streams;
+  h->w = w;
+  h->dc = make_divconst(w);
+  h->scale = scale_constant(h->dc);
+  e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(PRNG_ECUDA, "device attributes: %s", cudaGetErrorString(e));
+  }
+  e = cudaMalloc(&h->d_state, n_streams * sizeof(uint4));
+  if (e != cudaSuccess) {
+    delete h;
+    cudaGetLastError();
+    return fail(PRNG_ENOMEM, "cudaMalloc(state, %llu bytes): %s", (unsigned long long)(n_streams * 16),
+                cudaGetErrorString(e));
+  }
+  const unsigned blocks = (unsigned)((n_streams + 255) / 256);
+  prngd::seed_kernel<<<blocks, 256>>>(h->d_state, n_streams, seed);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) {
+    cudaFree(h->d_state);
+    delete h;
+    return fail(PRNG_ECUDA, "seeding: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return PRNG_OK;
+}
+
+int prng_destroy(prng_t h) {
+  if (!h) return PRNG_OK;
+  cudaDeviceSynchronize();
+  release_aux(h);
+  cudaFree(h->d_state);
+  delete h;
+  return PRNG_OK;
+}
+
+int prng_get_info(prng_t h, uint64_t* n_streams, int* w) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  if (n_streams) *n_streams = h->n_streams;
+  if (w) *w = h->w;
+  return PRNG_OK;
+}
+
+int prng_fill_f64(prng_t h, double* d_out, uint64_t per_stream, int form, uint64_t* d_rejects, void* cuda_stream) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS)
+    return fail(PRNG_EINVAL, "prng_fill_f64 takes form A (0) or B (1), got %d", form);
+  if (per_stream == 0) return PRNG_OK;
+  if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
+  if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
+  int rc = check_handle_device(h);
+  if (rc) return rc;
+  return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, form, d_rejects, (cudaStream_t)cuda_stream,
+                     true);
+}
+
+int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_rejects, void* cuda_stream) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  if (per_stream == 0) return PRNG_OK;
+  if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
+  if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
+  int rc = check_handle_device(h);
+  if (rc) return rc;
+  return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, PRNG_FORM_C_F32PAIR, d_rejects,
+                     (cudaStream_t)cuda_stream, true);
+}
+
+size_t prng_state_bytes(prng_t h) { return h ? (size_t)h->n_streams * 16 : 0; }
+
+int prng_state_save(prng_t h, void* host_buf, size_t bytes) {
+  if (!h || !host_buf) return fail(PRNG_EINVAL, "null argument");
+  if (bytes != prng_state_bytes(h)) return fail(PRNG_EINVAL, "bytes must be n_streams * 16");
+  cudaError_t e = cudaMemcpy(host_buf, h->d_state, bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "state save: %s", cudaGetErrorString(e));
+  return PRNG_OK;
+}
+
+int prng_state_restore(prng_t h, const void* host_buf, size_t bytes) {
+  if (!h || !host_buf) return fail(PRNG_EINVAL, "null argument");
+  if (bytes != prng_state_bytes(h)) return fail(PRNG_EINVAL, "bytes must be n_streams * 16");
+  cudaError_t e = cudaMemcpy(h->d_state, host_buf, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "state restore: %s", cudaGetErrorString(e));
+  return PRNG_OK;
+}
+
+int prng_fill_f64_host(prng_t h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS)
+    return fail(PRNG_EINVAL, "prng_fill_f64_host takes form A (0) or B (1), got %d", form);
+  if (per_stream == 0) return PRNG_OK;
+  if (!host_out) return fail(PRNG_EINVAL, "host_out is NULL");
+  int rc = check_handle_device(h);
+  if (rc) return rc;
+  return host_fill(h, host_out, per_stream, form, host_rejects);
+}
+
+}  // extern "C"

@@ -1,0 +1,32 @@
+// prngd_internal.h -- the handle behind prng_t and helpers shared by the library's
+// translation units. Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "prngd_math.cuh"
+
+struct prng_ctx {
+  int device;
+  uint64_t seed;
+  uint64_t n_streams;
+  int w;
+  uint4* d_state;       // n_streams xorshift128 states, resident between calls
+  prngd::DivConst dc;   // exact-division constants of D = (2^w - 1)^2
+  double scale;         // C_w = RN(1/D)
+  int num_sms;          // multiprocessors of the handle's device
+  // staging for prng_fill_f64_host (allocated on first use)
+  void* d_stage[2] = {nullptr, nullptr};
+  size_t stage_bytes = 0;
+  uint64_t* d_rej_stage = nullptr;
+  cudaStream_t io_stream[2] = {nullptr, nullptr};
+};
+
+namespace prngd_host {
+int fail(int code, const char* fmt, ...);
+int check_handle_device(prng_ctx* h);
+int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
+                uint64_t* rejects, cudaStream_t s, bool allow_tma);
+int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
+void release_aux(prng_ctx* h);
+}  // namespace prngd_host

@@ -1,0 +1,236 @@
+// prngd_math.cuh -- per-output arithmetic of the PRNGD construction (arXiv:1401.8230,
+// Section 2) for sm_103a: stream seeding, the xorshift128 base draws, the accept-reject
+// test, and the three conversions of the exact value z' = n / D to output bits.
+//
+// Notation: u1, u2 are w-bit draws, A = u1 - 1, B = u2 + 1, n = A 2^w + B (Eq. 4 reduced),
+// D = (2^w - 1)^2, V = n / D in [1/D, (D-1)/D]. V is never dyadic (D is odd and > n), so it
+// is never a tie for any rounding and never exactly representable.
+//
+// All functions are __host__ __device__ so the arithmetic can be exercised off the GPU too.
+#pragma once
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define PRNGD_HD __host__ __device__ __forceinline__
+#else
+#define PRNGD_HD inline
+#endif
+
+namespace prngd {
+
+// ------------------------------------------------------------------------ bit helpers
+PRNGD_HD int clz32(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  return __clz((int)v);
+#else
+  return v ? __builtin_clz(v) : 32;
+#endif
+}
+PRNGD_HD int clz64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)v);
+#else
+  return v ? __builtin_clzll(v) : 64;
+#endif
+}
+PRNGD_HD float bits_to_float(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(v);
+#else
+  float f;
+  __builtin_memcpy(&f, &v, 4);
+  return f;
+#endif
+}
+PRNGD_HD uint32_t float_to_bits(float f) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_uint(f);
+#else
+  uint32_t v;
+  __builtin_memcpy(&v, &f, 4);
+  return v;
+#endif
+}
+PRNGD_HD float int_to_float_rn(int32_t v) {
+#if defined(__CUDA_ARCH__)
+  return __int2float_rn(v);
+#else
+  return (float)v;
+#endif
+}
+PRNGD_HD float fmul_rn(float a, float b) {
+#if defined(__CUDA_ARCH__)
+  return __fmul_rn(a, b);
+#else
+  return a * b;
+#endif
+}
+PRNGD_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// ------------------------------------------------------------------------ base streams
+// splitmix64 (Steele, Lea, Flood 2014): the k-th output (k = 0, 1, ...) of the sequence
+// started at state `seed` is mix(seed + (k+1) * gamma), mix a bijective finaliser.
+constexpr uint64_t kGoldenGamma = 0x9E3779B97F4A7C15ull;
+
+PRNGD_HD uint64_t splitmix_finalise(uint64_t z) {
+  z ^= z >> 30;
+  z *= 0xBF58476D1CE4E5B9ull;
+  z ^= z >> 27;
+  z *= 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+struct XorShift128 {
+  uint32_t x, y, z, w;
+};
+
+// Stream s of `seed` takes splitmix64 outputs 2s and 2s+1, low word first. The finaliser maps
+// only 0 to 0 and its two inputs differ by gamma, so the state is never all zero.
+PRNGD_HD XorShift128 seed_stream(uint64_t seed, uint64_t s) {
+  const uint64_t o0 = splitmix_finalise(seed + (2 * s + 1) * kGoldenGamma);
+  const uint64_t o1 = splitmix_finalise(seed + (2 * s + 2) * kGoldenGamma);
+  return XorShift128{(uint32_t)o0, (uint32_t)(o0 >> 32), (uint32_t)o1, (uint32_t)(o1 >> 32)};
+}
+
+// Marsaglia (2003) xor128, shift triple (11, 8, 19); returns the new w word.
+PRNGD_HD uint32_t xs_next(XorShift128& s) {
+  const uint32_t t = s.x ^ (s.x << 11);
+  s.x = s.y;
+  s.y = s.z;
+  s.z = s.w;
+  s.w = s.w ^ (s.w >> 19) ^ (t ^ (t >> 8));
+  return s.w;
+}
+
+// A w-bit base draw: the top w bits of the 32-bit output (x = u 2^-w).
+template <int W>
+PRNGD_HD uint32_t draw(XorShift128& s, int w_rt) {
+  const uint32_t r = xs_next(s);
+  if constexpr (W == 32) {
+    return r;
+  } else if constexpr (W > 0) {
+    return r >> (32 - W);
+  } else {
+    return w_rt == 32 ? r : r >> (32 - w_rt);
+  }
+}
+
+// Accept-reject (Section 2): the pair is dropped when x1 = a0 (u1 = 0) or x1 = a
+// (u1 = 2^w - 1). One unsigned compare: u1 - 1 < 2^w - 2.
+PRNGD_HD bool accepted(uint32_t u1, uint32_t top /* 2^w - 1 */) { return (uint32_t)(u1 - 1u) < top - 1u; }
+
+PRNGD_HD uint64_t numerator(uint32_t u1, uint32_t u2, int w) {
+  return ((uint64_t)(u1 - 1u) << w) + (uint64_t)u2 + 1u;
+}
+
+// ------------------------------------------------------------------------ exact division
+// Constants for dividing by D without a hardware divide: D' = D << sh is D normalised to a
+// set top bit, and v = floor((2^128 - 1) / D') - 2^64 is its Moller-Granlund reciprocal
+// ("Improved division by invariant integers", IEEE Trans. Comput. 60(2), 2011, Alg. 4).
+struct DivConst {
+  uint64_t d_norm;  // D << sh
+  uint64_t v;       // reciprocal
+  int sh;           // 64 - 2w
+};
+
+// Double bits of RN(V) for any w in [2, 32], exactly. Normalise n to m = n 2^c in
+// [2^63, 2^64); Y = m / D' lies in (1/2, 2) and V = Y 2^(sh - c). The 2-by-1 division of
+// m 2^53 (Y >= 1) or m 2^54 (Y < 1) by D' gives the 54-bit integer part q of Y 2^53 or
+// Y 2^54; V is never a tie, so rounding to nearest is "round up iff the last bit of q is set".
+PRNGD_HD uint64_t rn_bits_exact(uint64_t n, const DivConst& dc) {
+  const int c = clz64(n);
+  const uint64_t m = n << c;
+  const bool ge = m >= dc.d_norm;
+  const int k = ge ? 53 : 54;
+  const uint64_t u1 = m >> (64 - k);  // < 2^54 <= D'
+  const uint64_t u0 = m << k;
+  // Algorithm 4 (div 2-by-1): q = floor((u1 2^64 + u0) / D'), with the remainder's two
+  // corrections.
+  uint64_t q0 = dc.v * u1;
+  uint64_t q1 = umulhi64(dc.v, u1);
+  const uint64_t s0 = q0 + u0;
+  q1 += u1 + (s0 < q0 ? 1u : 0u);
+  q0 = s0;
+  q1 += 1;
+  uint64_t r = u0 - q1 * dc.d_norm;
+  if (r > q0) {
+    q1 -= 1;
+    r += dc.d_norm;
+  }
+  if (r >= dc.d_norm) {
+    q1 += 1;
+    r -= dc.d_norm;
+  }
+  const uint64_t mant = (q1 >> 1) + (q1 & 1);  // in [2^52, 2^53]; 2^53 carries into the exponent
+  const int e = dc.sh - c - (ge ? 0 : 1);       // unbiased exponent of V
+  return ((uint64_t)(e + 1022) << 52) + mant;
+}
+
+// Double bits of RN(V) from I = floor(V 2^64) when I >= 2^54: the 54-bit integer part of
+// V 2^(53 - L) is I >> (L - 53) (nested floors), L = bit length of I minus one.
+PRNGD_HD uint64_t rn_bits_from_scaled(uint64_t I) {
+  const uint32_t ihi = (uint32_t)(I >> 32);  // >= 2^22
+  const int p = 31 - clz32(ihi);             // L - 32, in [22, 31]
+  const uint64_t q = I >> (p - 21);          // in [2^53, 2^54)
+  const uint64_t mant = (q >> 1) + (q & 1);
+  return ((uint64_t)(p + 990) << 52) + mant;  // exponent L - 64, biased: L + 959, minus 1 for mant
+}
+
+// Fast path for w = 32. With eps = 2^-32,
+//   V 2^64 = n / (1 - eps)^2 = A 2^32 + (B + 2A) + sum_{j>=1} ((j+1) B + (j+2) A) eps^j,
+// and the tail beyond j = 1 is below 7.01 eps. With X = 2B + 3A (35 bits) the integer part is
+// I = A 2^32 + B + 2A + (X >> 32) unless the low word of X is within 8 of 2^32. Needs
+// A >= 2^22 so that I >= 2^54. fast32_ok says whether the fast path applies (it also
+// rejects u1 = 0 and u1 = 2^32 - 1, which the caller's slow path handles).
+PRNGD_HD uint64_t fast32_X(uint32_t u1, uint32_t u2) { return (uint64_t)u1 * 3u + (uint64_t)u2 * 2u - 1u; }
+PRNGD_HD bool fast32_ok(uint32_t u1, uint64_t X) {
+  return ((uint32_t)(u1 - 0x400001u) < 0xFFBFFFFEu) & ((uint32_t)X < 0xFFFFFFF8u);  // 2^22 <= A <= 2^32-3
+}
+PRNGD_HD uint64_t fast32_bits(uint32_t u1, uint32_t u2, uint64_t X) {
+  const uint64_t I = ((uint64_t)(u1 - 1u) << 32) + (uint64_t)u1 * 2u + (uint64_t)u2 - 1u + (X >> 32);
+  return rn_bits_from_scaled(I);
+}
+
+// Fast path for w = 24. With eps = 2^-24,
+//   V 2^64 = A 2^40 + (B + 2A) 2^16 + (2B + 3A) 2^-8 + (3B + 4A) 2^-32 + tail,
+// tail < 9.01 2^-32. With K = (2B + 3A) 2^24 + (3B + 4A) (< 2^51) the integer part is
+// I = A 2^40 + (B + 2A) 2^16 + (K >> 32) unless the low word of K is within 16 of 2^32.
+// Needs A >= 2^14 so that I >= 2^54.
+PRNGD_HD uint64_t fast24_K(uint32_t u1, uint32_t u2) {
+  const uint32_t A = u1 - 1u, B = u2 + 1u;
+  return ((uint64_t)(2u * B + 3u * A) << 24) + (uint64_t)(3u * B + 4u * A);
+}
+PRNGD_HD bool fast24_ok(uint32_t u1, uint64_t K) {
+  return ((uint32_t)(u1 - 1u - 0x4000u) < 0xFFBFFEu) & ((uint32_t)K < 0xFFFFFFF0u);  // 2^14 <= A <= 2^24-3
+}
+PRNGD_HD uint64_t fast24_bits(uint32_t u1, uint32_t u2, uint64_t K) {
+  const uint32_t A = u1 - 1u, B = u2 + 1u;
+  const uint64_t I = ((uint64_t)A << 40) + ((uint64_t)(B + 2u * A) << 16) + (K >> 32);
+  return rn_bits_from_scaled(I);
+}
+
+// Form C from the form-B bits d: hi = RN32(d) by rounding the 53-bit significand to 24 bits
+// (round half to even; d is dyadic so ties occur), lo = RN32(d - hi) where d - hi = R 2^(e-52)
+// exactly for the signed integer R = (low 29 bits) - 2^29 * (rounded up). Packed as
+// (lo bits << 32) | hi bits, i.e. hi first in memory.
+PRNGD_HD uint64_t f32pair_from_bits(uint64_t d) {
+  const uint32_t rem = (uint32_t)d & 0x1FFFFFFFu;
+  const uint32_t top = (uint32_t)(d >> 29);  // sign | exp11 | 23 fraction bits
+  const uint32_t up = (rem > 0x10000000u) || (rem == 0x10000000u && (top & 1u));
+  const uint32_t hi = top - (896u << 23) + up;  // rebias 1023 -> 127
+  const int32_t R = (int32_t)rem - (int32_t)(up << 29);
+  const int e = (int)((d >> 52) & 0x7FF) - 1023;
+  // lo = RN24(R) * 2^(e-52): the integer-to-float conversion rounds R to nearest even, and
+  // the power-of-two scale is exact (e - 52 >= -116, inside the float normal range).
+  const float scale = bits_to_float((uint32_t)(e - 52 + 127) << 23);
+  const float lo = fmul_rn(int_to_float_rn(R), scale);
+  return ((uint64_t)float_to_bits(lo) << 32) | hi;
+}
+
+}  // namespace prngd

@@ -1,0 +1,59 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every function declared in
+include/prngd.h, and rejects bad arguments on the host (no GPU needed for those paths)."""
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+import paper_1401_8230_gb300 as P
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w \*]*?\b(prng_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("prng_create", "prng_destroy", "prng_fill_f64", "prng_fill_f32pair",
+                     "prng_state_save", "prng_state_restore"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = P.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+    assert P.prng_version() >= 100
+
+
+@pytest.mark.parametrize("kwargs, fragment", [
+    (dict(seed=1, n_streams=64, w=1), "outside [2, 32]"),
+    (dict(seed=1, n_streams=64, w=33), "outside [2, 32]"),
+    (dict(seed=1, n_streams=0, w=32), "n_streams"),
+    (dict(seed=1, n_streams=2**32 + 1, w=32), "n_streams"),
+    (dict(seed=1, n_streams=8, w=32, a0=0.0, a=1.0), "a - a0"),
+    (dict(seed=1, n_streams=8, w=24, b0=0.5, b=1.0), "a - a0"),
+    (dict(seed=1, n_streams=8, w=16, a0=float("nan")), "finite"),
+])
+def test_create_rejects_bad_arguments_on_the_host(kwargs, fragment):
+    with pytest.raises(P.PrngError) as ei:
+        P.prng_create(**kwargs)
+    assert ei.value.code == P.PRNG_EINVAL
+    assert fragment in str(ei.value)
+
+
+def test_null_handle_is_rejected():
+    with pytest.raises(P.PrngError) as ei:
+        P.prng_fill_f64(0, 0, 16, P.FORM_B_INTBITS)
+    assert ei.value.code == P.PRNG_EINVAL
+    assert P.prng_state_bytes(0) == 0
+    P.prng_destroy(0)  # no-op
