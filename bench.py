@@ -43,10 +43,14 @@ KERNEL_SOURCES = ["paper_1401_8230_gb300/csrc/prngd_fill.cuh", "paper_1401_8230_
 
 
 def workload_desc():
-    return {"workload": "bulk fill: 2^20 xorshift128 streams (seed 1) x 1024 outputs = 2^30 uniforms, "
-                        "w=32, form B (correctly rounded f64, integer-only), stream-major, 8 GiB, one launch",
+    if (N_STREAMS, PER_STREAM) == (1 << 20, 1024):
+        name = ("bulk fill: 2^20 xorshift128 streams (seed 1) x 1024 outputs = 2^30 uniforms, "
+                "w=32, form B (correctly rounded f64, integer-only), stream-major, 8 GiB, one launch")
+    else:
+        name = f"reduced bulk fill: {N_STREAMS} streams x {PER_STREAM} outputs, w=32, form B (profiling case)"
+    return {"workload": name,
             "n_streams": N_STREAMS, "per_stream": PER_STREAM, "w": W, "form": "B", "output": "f64",
-            "l2": "8 GiB output per step > 129 MB L2: no flush"}
+            "l2": f"{N_STREAMS * PER_STREAM * 8 / 2**30:.2f} GiB output per step > 129 MB L2: no flush"}
 
 
 def kernel_hash():
@@ -156,8 +160,8 @@ def oracle_rate(n_streams_sample: int, first: int = 0, threads: int | None = Non
 
 def cpu_baseline(target_s: float = 10.0):
     # calibrate on a small sample, then time a sample sized for ~target_s of wall time
-    rate, _, threads = oracle_rate(256)
-    n = int(max(256, min(N_STREAMS, rate * 1e9 * target_s / PER_STREAM)))
+    rate, _, threads = oracle_rate(2048)
+    n = int(max(2048, min(N_STREAMS, rate * 1e9 * target_s / PER_STREAM)))
     rate, dt, threads = oracle_rate(n)
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"streams 0..{n - 1} of the bulk workload (seed 1, w=32, form B, 1024 outputs each; "
@@ -169,8 +173,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    rate, _, threads = oracle_rate(256)
-    n = int(max(256, min(N_STREAMS, rate * 1e9 * 2.0 / PER_STREAM)))  # ~2 s per step
+    rate, _, threads = oracle_rate(2048)
+    per_step_s = min(2.0, 120.0 / (args.steps + args.warmup))  # whole run within ~2 minutes
+    n = int(max(64, min(N_STREAMS, rate * 1e9 * per_step_s / PER_STREAM)))
     for _ in range(args.warmup):
         oracle_rate(max(64, n // 8))
     times, total = [], 0
@@ -211,7 +216,13 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-streams", type=int, default=None, help="override the stream count (profiling runs)")
+    ap.add_argument("--per-stream", type=int, default=None, help="override outputs per stream (profiling runs)")
     args = ap.parse_args()
+    global N_STREAMS, PER_STREAM
+    N_STREAMS = args.n_streams or N_STREAMS
+    PER_STREAM = args.per_stream or PER_STREAM
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
@@ -284,7 +295,7 @@ def main():
 
     if rank == 0 and not args.no_extras:
         line["forms"] = extras(torch, P, g, out, stream, peak)
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(torch, P, g, samples_step)
     del out
     g.close()
