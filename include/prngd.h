@@ -115,6 +115,34 @@ int prng_fill_f64_host(prng_t h, double* host_out, uint64_t per_stream, int form
                        uint64_t* host_rejects);
 
 /*
+ * prng_fill_f64_host_noalloc -- the paper has no counterpart; this is a library convenience.
+ * Same values, reject counts and stream advance as prng_fill_f64_host, but the call
+ * allocates nothing: no cudaMalloc, no cudaFree, no pinned buffers, no streams. It is for
+ * callers that cannot allocate device memory when they need numbers. Examples: a process
+ * whose GPU memory already belongs to another allocator (a framework pool that reserved the
+ * device), a service that fixes its footprint at start-up and must not fail with
+ * out-of-memory later, or a loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc/cudaFree may cause. (prng_create still allocates the stream state, once.)
+ * Device staging is a fixed array inside the library of PRNG_NOALLOC_VALUE_BYTES +
+ * 8 * PRNG_NOALLOC_MAX_SLICE_STREAMS bytes (17 MiB); every GPU that loads the library holds
+ * it until the process exits.
+ * Work runs on `cuda_stream` (NULL = legacy default stream) in slices that fit the array,
+ * one after another; the call synchronises that stream before returning. The first call on a
+ * device looks up the array's device address (once per device); make that first call
+ * before any stream capture.
+ * All calls share the one array, and it keeps the last call's contents. Calls that overlap
+ * on the GPU (two host threads, or two streams, on the same device) race on it and give
+ * wrong results; serialise them.
+ * Limits: per_stream <= PRNG_NOALLOC_VALUE_BYTES / 8 (2^21 outputs per stream); larger
+ * values return PRNG_EINVAL with the limit in prng_last_error().
+ * Errors: PRNG_EINVAL, PRNG_ECUDA.
+ */
+#define PRNG_NOALLOC_VALUE_BYTES ((size_t)16 << 20)
+#define PRNG_NOALLOC_MAX_SLICE_STREAMS ((uint64_t)1 << 17)
+int prng_fill_f64_host_noalloc(prng_t h, double* host_out, uint64_t per_stream, int form,
+                               uint64_t* host_rejects, void* cuda_stream);
+
+/*
  * prng_fused_stats -- generate per_stream outputs of every stream (advancing the streams
  * exactly as a fill would) and reduce them without storing any value: a 65536-bin
  * histogram of floor(2^16 z') and the four sums S1 = sum t, S2 = sum p2, S3 = sum p3,

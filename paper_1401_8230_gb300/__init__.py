@@ -24,6 +24,7 @@ from ._binding import (  # noqa: F401
     prng_fill_f32pair,
     prng_fill_f64,
     prng_fill_f64_host,
+    prng_fill_f64_host_noalloc,
     prng_fused_stats,
     prng_get_info,
     prng_last_error,

@@ -26,6 +26,7 @@ _SIGNATURES = {
     "prng_fill_f64": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fill_f32pair": (_i32, [_P, _vp, _u64, _vp, _vp]),
     "prng_fill_f64_host": (_i32, [_P, _vp, _u64, _i32, _vp]),
+    "prng_fill_f64_host_noalloc": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
     "prng_state_bytes": (_sz, [_P]),
     "prng_state_save": (_i32, [_P, _vp, _sz]),
@@ -126,6 +127,11 @@ def prng_fill_f32pair(h: int, out, per_stream: int, rejects=None, stream=None) -
 
 def prng_fill_f64_host(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None) -> None:
     _check(lib().prng_fill_f64_host(h, _ptr(out), per_stream, form, _ptr(rejects)))
+
+
+def prng_fill_f64_host_noalloc(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None,
+                               stream=None) -> None:
+    _check(lib().prng_fill_f64_host_noalloc(h, _ptr(out), per_stream, form, _ptr(rejects), _stream(stream)))
 
 
 def prng_fused_stats(h: int, per_stream: int, hist, sums, rejects=None, stream=None) -> None:
