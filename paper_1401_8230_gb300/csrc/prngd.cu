@@ -86,7 +86,7 @@ bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t pe
 
 // ----------------------------------------------------------------- fill dispatch
 constexpr int kWarpsPerBlock = 8;
-constexpr int kNbuf = 2;
+constexpr int kNbuf = 1;  // one tile per warp: 4 blocks of 8 warps fit per SM (registers and shared memory)
 constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * kNbuf * prngd::kTileBytes + 1024;
 
 template <int W, int FORM>
@@ -127,6 +127,7 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
   p.dc = h->dc;
   p.scale = h->scale;
   p.w = h->w;
+  p.one = 1;
   CUtensorMap map;
   const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
   cudaError_t e;

@@ -24,6 +24,7 @@ struct FillParams {
   DivConst dc;          // exact-division constants of D
   double scale;         // C_w = RN(1/D) for form A
   int w;                // draw precision
+  uint32_t one;         // always 1; a run-time multiplier keeps the adds below on the FMA pipe
 };
 
 // ------------------------------------------------------------------------ per-output work
@@ -80,6 +81,120 @@ __device__ __forceinline__ uint64_t next_output(XorShift128& st, uint32_t& rej, 
   return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }
 
+// ------------------------------------------------------------------------ pair fast path
+// Four consecutive draws in place: each state word is replaced once, so after the block
+// (x, y, z, w) is again the state in its usual order and the four draws are its words.
+__device__ __forceinline__ uint32_t xs_word(uint32_t a, uint32_t w) {
+  const uint32_t t = a ^ (a << 11);
+  return w ^ (w >> 19) ^ (t ^ (t >> 8));
+}
+__device__ __forceinline__ void xs_block4(XorShift128& s) {
+  s.x = xs_word(s.x, s.w);
+  s.y = xs_word(s.y, s.x);
+  s.z = xs_word(s.z, s.y);
+  s.w = xs_word(s.w, s.z);
+}
+
+// The w = 32 form-B fast path of fast32_ok / fast32_bits written out as PTX, with the adds
+// that need no carry issued as multiply-adds by the run-time constant `one` so that they run
+// on the FMA pipe beside the ALU work of the draws. Returns 1 in `ok` when the fast path
+// applies (same condition as fast32_ok); the value is meaningless otherwise.
+__device__ __forceinline__ uint64_t fast32_bits_ptx(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
+  uint32_t lo, hi;
+  asm("{\n\t"
+      ".reg .u64 Y, X, P, Ip;\n\t"
+      ".reg .u32 xlo, f, a, A, g, ilo, ihi, q, s, rb, jlo, jhi, s1, mhi, e;\n\t"
+      ".reg .pred p1, p2;\n\t"
+      "mad.wide.u32 Y, %4, 2, -1;\n\t"           // 2 u2 - 1
+      "mad.wide.u32 X, %3, 3, Y;\n\t"            // X = 2B + 3A = 3 u1 + 2 u2 - 1
+      "mov.b64 {xlo, f}, X;\n\t"
+      "mad.lo.u32 a, %3, %5, -4194305;\n\t"      // u1 - (2^22 + 1)
+      "setp.lt.u32 p1, a, 0xFFBFFFFD;\n\t"       // 2^22 <= A <= 2^32 - 4
+      "setp.lt.and.u32 p2, xlo, 0xFFFFFFF8, p1;\n\t"
+      "selp.u32 %1, 1, 0, p2;\n\t"
+      "mad.lo.u32 A, %3, %5, -1;\n\t"            // A = u1 - 1
+      "mov.b64 P, {%4, A};\n\t"
+      "mad.wide.u32 Ip, A, 2, P;\n\t"            // A 2^32 + u2 + 2A
+      "mad.lo.u32 g, f, %5, 1;\n\t"
+      "mov.b64 {ilo, ihi}, Ip;\n\t"
+      "add.cc.u32 ilo, ilo, g;\n\t"              // I = A 2^32 + B + 2A + (X >> 32)
+      "addc.u32 ihi, ihi, 0;\n\t"
+      "bfind.u32 q, ihi;\n\t"                    // p, top bit of the high word
+      "mad.lo.u32 s, q, %5, -21;\n\t"
+      "shl.b32 rb, 1, s;\n\t"
+      "add.cc.u32 jlo, ilo, rb;\n\t"             // J = I + 2^s
+      "addc.u32 jhi, ihi, 0;\n\t"
+      "mad.lo.u32 s1, q, %5, -20;\n\t"
+      "shf.r.wrap.b32 %2, jlo, jhi, s1;\n\t"     // mantissa, low word
+      "shr.u32 mhi, jhi, s1;\n\t"
+      "mad.lo.u32 e, q, 0x100000, 0x3DE00000;\n\t"  // (p + 990) << 20
+      "mad.lo.u32 %0, mhi, %5, e;\n\t"
+      "}"
+      : "=r"(hi), "=r"(ok), "=r"(lo)
+      : "r"(u1), "r"(u2), "r"(one));
+  return ((uint64_t)hi << 32) | lo;
+}
+
+struct PairOut {
+  uint64_t v0, v1;
+  uint32_t x, y, z, w, rej;
+};
+
+// Exact replay of two outputs from state (x, y, z, w): in-order rejects, exact conversion.
+template <int FORM>
+__device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t rej, int wbits,
+                                          DivConst dc) {
+  XorShift128 st{x, y, z, w};
+  const uint32_t top = (wbits == 32) ? 0xFFFFFFFFu : ((1u << wbits) - 1u);
+  uint64_t v[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    uint32_t u1 = draw<0>(st, wbits), u2 = draw<0>(st, wbits);
+    while (!accepted(u1, top)) {
+      ++rej;
+      u1 = draw<0>(st, wbits);
+      u2 = draw<0>(st, wbits);
+    }
+    const uint64_t bits = rn_bits_exact(numerator(u1, u2, wbits), dc);
+    v[k] = FORM == kFormC ? f32pair_from_bits(bits) : bits;
+  }
+  return PairOut{v[0], v[1], st.x, st.y, st.z, st.w, rej};
+}
+
+// Two outputs of a w = 32 or w = 24 stream (forms B and C) from one 4-draw block, with one
+// branch for the pair: when either output needs the exact path, the pair is replayed from
+// the block's starting state.
+template <int W, int FORM>
+__device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const FillParams& p, uint64_t& v0,
+                                          uint64_t& v1) {
+  const XorShift128 old = st;
+  xs_block4(st);
+  uint32_t ok;
+  if constexpr (W == 32) {
+    uint32_t ok0, ok1;
+    v0 = fast32_bits_ptx(st.x, st.y, p.one, ok0);
+    v1 = fast32_bits_ptx(st.z, st.w, p.one, ok1);
+    ok = ok0 & ok1;
+  } else {
+    const uint32_t u1a = st.x >> 8, u2a = st.y >> 8, u1b = st.z >> 8, u2b = st.w >> 8;
+    const uint64_t Ka = fast24_K(u1a, u2a), Kb = fast24_K(u1b, u2b);
+    ok = fast24_ok(u1a, Ka) & fast24_ok(u1b, Kb);
+    v0 = fast24_bits(u1a, u2a, Ka);
+    v1 = fast24_bits(u1b, u2b, Kb);
+  }
+  if (FORM == kFormC) {
+    v0 = f32pair_from_bits(v0);
+    v1 = f32pair_from_bits(v1);
+  }
+  if (__builtin_expect(ok == 0, 0)) {
+    const PairOut o = slow_pair<FORM>(old.x, old.y, old.z, old.w, rej, W, p.dc);
+    v0 = o.v0;
+    v1 = o.v1;
+    rej = o.rej;
+    st = XorShift128{o.x, o.y, o.z, o.w};
+  }
+}
+
 // ------------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -118,7 +233,7 @@ __global__ void seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
 // and columns past per_stream fall outside the tensor and are not written. NBUF tiles per
 // warp let the next chunk's staging proceed while the previous store still reads shared memory.
 template <int W, int FORM, int NBUF>
-__global__ void __launch_bounds__(256) fill_tma_kernel(const FillParams p,
+__global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
                                                        const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (smem_addr(smem_raw) + 1023u) & ~1023u;
@@ -140,8 +255,13 @@ __global__ void __launch_bounds__(256) fill_tma_kernel(const FillParams p,
     uint64_t v[kChunk];
     const uint64_t left = p.per_stream - x0;
     if (left >= (uint64_t)kChunk) {
+      if constexpr ((W == 32 || W == 24) && FORM != kFormA) {
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) v[j] = next_output<W, FORM>(st, rej, p);
+        for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM>(st, rej, p, v[j], v[j + 1]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) v[j] = next_output<W, FORM>(st, rej, p);
+      }
     } else {
 #pragma unroll
       for (int j = 0; j < kChunk; ++j) v[j] = (j < (int)left) ? next_output<W, FORM>(st, rej, p) : 0ull;

@@ -65,6 +65,24 @@ PRNGD_HD float fmul_rn(float a, float b) {
   return a * b;
 #endif
 }
+// a * b + c with a 64-bit result (one wide multiply-add).
+PRNGD_HD uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c) {
+#if defined(__CUDA_ARCH__)
+  uint64_t d;
+  asm("mad.wide.u32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+#else
+  return (uint64_t)a * b + c;
+#endif
+}
+// (hi:lo) >> s, low word, for 0 <= s < 32.
+PRNGD_HD uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t s) {
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(lo, hi, s);
+#else
+  return (uint32_t)((((uint64_t)hi << 32) | lo) >> (s & 31));
+#endif
+}
 PRNGD_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
 #if defined(__CUDA_ARCH__)
   return __umul64hi(a, b);
@@ -106,6 +124,20 @@ PRNGD_HD uint32_t xs_next(XorShift128& s) {
   s.z = s.w;
   s.w = s.w ^ (s.w >> 19) ^ (t ^ (t >> 8));
   return s.w;
+}
+
+// The inverse step: the state before the last xs_next. With (x, y, z, w) the current state,
+// the previous one is (x0, x, y, z) where t = x0 ^ (x0 << 11) satisfies t ^ (t >> 8) =
+// w ^ z ^ (z >> 19); both xor-shifts are inverted by repeating them until the shift passes
+// 32 bits.
+PRNGD_HD void xs_prev(XorShift128& s) {
+  const uint32_t r = s.w ^ s.z ^ (s.z >> 19);
+  const uint32_t t = r ^ (r >> 8) ^ (r >> 16) ^ (r >> 24);
+  const uint32_t x0 = t ^ (t << 11) ^ (t << 22);
+  s.w = s.z;
+  s.z = s.y;
+  s.y = s.x;
+  s.x = x0;
 }
 
 // A w-bit base draw: the top w bits of the 32-bit output (x = u 2^-w).
@@ -186,15 +218,27 @@ PRNGD_HD uint64_t rn_bits_from_scaled(uint64_t I) {
 //   V 2^64 = n / (1 - eps)^2 = A 2^32 + (B + 2A) + sum_{j>=1} ((j+1) B + (j+2) A) eps^j,
 // and the tail beyond j = 1 is below 7.01 eps. With X = 2B + 3A (35 bits) the integer part is
 // I = A 2^32 + B + 2A + (X >> 32) unless the low word of X is within 8 of 2^32. Needs
-// A >= 2^22 so that I >= 2^54. fast32_ok says whether the fast path applies (it also
-// rejects u1 = 0 and u1 = 2^32 - 1, which the caller's slow path handles).
+// A >= 2^22 so that I >= 2^54, and A <= 2^32 - 4 so that I + 2^10 < 2^64 (the largest values,
+// which round to 1.0, take the exact path). fast32_ok says whether the fast path applies (it
+// also rejects u1 = 0 and u1 = 2^32 - 1, which the caller's slow path handles).
 PRNGD_HD uint64_t fast32_X(uint32_t u1, uint32_t u2) { return (uint64_t)u1 * 3u + (uint64_t)u2 * 2u - 1u; }
 PRNGD_HD bool fast32_ok(uint32_t u1, uint64_t X) {
-  return ((uint32_t)(u1 - 0x400001u) < 0xFFBFFFFEu) & ((uint32_t)X < 0xFFFFFFF8u);  // 2^22 <= A <= 2^32-3
+  return ((uint32_t)(u1 - 0x400001u) < 0xFFBFFFFDu) & ((uint32_t)X < 0xFFFFFFF8u);  // 2^22 <= A <= 2^32-4
 }
 PRNGD_HD uint64_t fast32_bits(uint32_t u1, uint32_t u2, uint64_t X) {
-  const uint64_t I = ((uint64_t)(u1 - 1u) << 32) + (uint64_t)u1 * 2u + (uint64_t)u2 - 1u + (X >> 32);
-  return rn_bits_from_scaled(I);
+  // I = (u1 - 1) 2^32 + (2 u1 + u2 - 1 + (X >> 32)), in 32-bit words.
+  const uint64_t L = (uint64_t)u1 * 2u + (uint64_t)u2 + (X >> 32) - 1u;  // < 2^35
+  const uint32_t ilo = (uint32_t)L;
+  const uint32_t ihi = (u1 - 1u) + (uint32_t)(L >> 32);  // >= 2^22
+  // Round at bit s = L - 53 of I (L = 32 + p its top bit) by adding 2^s, then keep the 53 bits
+  // above it; a carry out of the top is the next binade (exponent + 1, mantissa 0).
+  const uint32_t p = 31u - (uint32_t)clz32(ihi);  // in [22, 31]
+  const uint32_t s = p - 21u;                       // in [1, 10]
+  const uint32_t jlo = ilo + (1u << s);
+  const uint32_t jhi = ihi + (jlo < ilo ? 1u : 0u);
+  const uint32_t mlo = funnel_r(jlo, jhi, s + 1u);
+  const uint32_t mhi = (jhi >> (s + 1u)) + ((p + 990u) << 20);  // biased exponent L - 64, minus the implicit 1
+  return ((uint64_t)mhi << 32) | mlo;
 }
 
 // Fast path for w = 24. With eps = 2^-24,
@@ -211,8 +255,18 @@ PRNGD_HD bool fast24_ok(uint32_t u1, uint64_t K) {
 }
 PRNGD_HD uint64_t fast24_bits(uint32_t u1, uint32_t u2, uint64_t K) {
   const uint32_t A = u1 - 1u, B = u2 + 1u;
-  const uint64_t I = ((uint64_t)A << 40) + ((uint64_t)(B + 2u * A) << 16) + (K >> 32);
-  return rn_bits_from_scaled(I);
+  // I = A 2^40 + (B + 2A) 2^16 + (K >> 32), in 32-bit words: the high word is A 2^8 plus the
+  // carry out of the low 48-bit sum.
+  const uint64_t L = ((uint64_t)(B + 2u * A) << 16) + (K >> 32);  // < 2^42
+  const uint32_t ilo = (uint32_t)L;
+  const uint32_t ihi = (A << 8) + (uint32_t)(L >> 32);  // >= 2^22
+  const uint32_t p = 31u - (uint32_t)clz32(ihi);
+  const uint32_t s = p - 21u;
+  const uint32_t jlo = ilo + (1u << s);
+  const uint32_t jhi = ihi + (jlo < ilo ? 1u : 0u);
+  const uint32_t mlo = funnel_r(jlo, jhi, s + 1u);
+  const uint32_t mhi = (jhi >> (s + 1u)) + ((p + 990u) << 20);
+  return ((uint64_t)mhi << 32) | mlo;
 }
 
 // Form C from the form-B bits d: hi = RN32(d) by rounding the 53-bit significand to 24 bits
