@@ -158,6 +158,67 @@ int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist, uint64_t* 
                      uint64_t* d_rejects, void* cuda_stream);
 
 /*
+ * Batched requests. Many fill requests of uneven length run in one persistent launch over a
+ * device work queue (a counter over items of 32 rows), replayed from a CUDA graph captured
+ * once per launch shape. Each request's output is a stream-major block of rows, row j being
+ * one stream's outputs in order (Section 2's construction per output, as in the fills):
+ *
+ *  PRNG_REQ_FRESH:    rows are streams first_stream + j of `seed` (seeded as in prng_create),
+ *                     `chunk` outputs each (even; 0 means 1024), the last row shorter;
+ *                     ceil(length / chunk) streams. Stateless: the same request always gives
+ *                     the same output.
+ *  PRNG_REQ_RESIDENT: rows continue the handle's streams first_stream .. first_stream +
+ *                     n_streams - 1 (device-resident state, advanced by the call). Row length
+ *                     per = 2 * ceil(length / (2 * n_streams)); row j holds
+ *                     min(per, max(0, length - j * per)) outputs.
+ *
+ * The outputs never depend on the launch shape, on the batch a request is in, or on the
+ * other requests of the batch. d_out: device pointer, 16-byte aligned, 8 * length bytes
+ * (form C: interleaved float pairs). d_rejects (nullable, device): one reject count per row.
+ */
+#define PRNG_REQ_FRESH 0
+#define PRNG_REQ_RESIDENT 1
+#define PRNG_MAX_BATCH_REQUESTS 4096
+
+typedef struct prng_request {
+  int32_t kind;          /* PRNG_REQ_FRESH or PRNG_REQ_RESIDENT */
+  int32_t form;          /* PRNG_FORM_A_FP64, PRNG_FORM_B_INTBITS or PRNG_FORM_C_F32PAIR */
+  uint64_t length;       /* outputs, >= 1 */
+  uint64_t seed;         /* FRESH: seed of the request's streams */
+  uint64_t first_stream; /* FRESH: first stream id; RESIDENT: first stream of the handle */
+  uint64_t n_streams;    /* RESIDENT: streams of the handle to continue (FRESH: ignored) */
+  uint32_t chunk;        /* FRESH: outputs per stream, even (0 = 1024); RESIDENT: ignored */
+  uint32_t reserved;     /* 0 */
+  void* d_out;           /* device pointer, 16-byte aligned */
+  uint64_t* d_rejects;   /* nullable device pointer, one count per row */
+} prng_request;
+
+/*
+ * prng_submit -- enqueue a batch of 1 .. PRNG_MAX_BATCH_REQUESTS requests on `cuda_stream`
+ * and return a ticket. The call copies the descriptors, so `reqs` may be reused at once.
+ * Resident requests of one batch must not share streams; batches on different CUDA streams
+ * that use the same resident streams must be ordered by the caller.
+ * Errors: PRNG_EINVAL (bad request, overlapping resident ranges, n out of range),
+ * PRNG_EBUSY (all 4 batch slots still in flight: poll or wait, then retry), PRNG_ENOMEM,
+ * PRNG_ECUDA.
+ */
+int prng_submit(prng_t h, const prng_request* reqs, int n, uint64_t* ticket, void* cuda_stream);
+
+/* prng_poll -- *done = 1 if the batch of `ticket` has finished on the device, else 0.
+ * Non-blocking. Errors: PRNG_ENOTFOUND (a ticket this handle never issued), PRNG_ECUDA. */
+int prng_poll(prng_t h, uint64_t ticket, int* done);
+
+/* prng_wait -- block (polling) until the batch of `ticket` has finished, at most timeout_s
+ * seconds. Errors: PRNG_ETIMEOUT, PRNG_ENOTFOUND, PRNG_ECUDA. */
+int prng_wait(prng_t h, uint64_t ticket, double timeout_s);
+
+/* Launch shape of the batch kernel: warps per block (1..8), blocks per SM (1..16) and items
+ * taken per counter increment (1..64). Changing it never changes outputs; set_shape waits
+ * for in-flight batches and re-captures the graphs on next use. */
+int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket);
+int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket);
+
+/*
  * State checkpoint: each stream's state is 16 bytes (xorshift128 words x, y, z, w).
  * prng_state_bytes gives n_streams * 16. save copies the device state into host_buf and
  * restore copies it back; both synchronise. A fill after restore reproduces the outputs

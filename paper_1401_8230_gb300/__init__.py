@@ -17,8 +17,15 @@ from ._binding import (  # noqa: F401
     PRNG_ETIMEOUT,
     PRNG_OK,
     Generator,
+    MAX_BATCH_REQUESTS,
+    REQ_FRESH,
+    REQ_RESIDENT,
     PrngError,
+    Request,
+    fresh_request,
     lib,
+    prng_batch_get_shape,
+    prng_batch_set_shape,
     prng_create,
     prng_destroy,
     prng_fill_f32pair,
@@ -28,8 +35,12 @@ from ._binding import (  # noqa: F401
     prng_fused_stats,
     prng_get_info,
     prng_last_error,
+    prng_poll,
     prng_state_bytes,
     prng_state_restore,
     prng_state_save,
+    prng_submit,
     prng_version,
+    prng_wait,
+    resident_request,
 )

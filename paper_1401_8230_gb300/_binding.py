@@ -9,6 +9,24 @@ from . import build as _build
 
 PRNG_OK, PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA, PRNG_ETIMEOUT, PRNG_EBUSY, PRNG_ENOTFOUND = range(7)
 FORM_A_FP64, FORM_B_INTBITS, FORM_C_F32PAIR = 0, 1, 2
+REQ_FRESH, REQ_RESIDENT = 0, 1
+MAX_BATCH_REQUESTS = 4096
+
+
+class Request(ctypes.Structure):
+    """struct prng_request of include/prngd.h."""
+    _fields_ = [("kind", ctypes.c_int32), ("form", ctypes.c_int32), ("length", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("first_stream", ctypes.c_uint64), ("n_streams", ctypes.c_uint64),
+                ("chunk", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("d_out", ctypes.c_void_p),
+                ("d_rejects", ctypes.c_void_p)]
+
+
+def fresh_request(out, length: int, seed: int, first_stream: int, form: int = 1, chunk: int = 0, rejects=None):
+    return Request(REQ_FRESH, form, length, seed & (2**64 - 1), first_stream, 0, chunk, 0, _ptr(out), _ptr(rejects))
+
+
+def resident_request(out, length: int, first_stream: int, n_streams: int, form: int = 1, rejects=None):
+    return Request(REQ_RESIDENT, form, length, 0, first_stream, n_streams, 0, 0, _ptr(out), _ptr(rejects))
 
 _lock = threading.Lock()
 _lib: ctypes.CDLL | None = None
@@ -29,6 +47,11 @@ _SIGNATURES = {
     "prng_fill_f64_host_noalloc": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
     "prng_state_bytes": (_sz, [_P]),
+    "prng_submit": (_i32, [_P, ctypes.c_void_p, _i32, ctypes.POINTER(_u64), _vp]),
+    "prng_poll": (_i32, [_P, _u64, ctypes.POINTER(_i32)]),
+    "prng_wait": (_i32, [_P, _u64, _dbl]),
+    "prng_batch_get_shape": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "prng_batch_set_shape": (_i32, [_P, _i32, _i32, _i32]),
     "prng_state_save": (_i32, [_P, _vp, _sz]),
     "prng_state_restore": (_i32, [_P, _vp, _sz]),
 }
@@ -136,6 +159,35 @@ def prng_fill_f64_host_noalloc(h: int, out, per_stream: int, form: int = FORM_B_
 
 def prng_fused_stats(h: int, per_stream: int, hist, sums, rejects=None, stream=None) -> None:
     _check(lib().prng_fused_stats(h, per_stream, _ptr(hist), _ptr(sums), _ptr(rejects), _stream(stream)))
+
+
+def prng_submit(h: int, reqs, stream=None) -> int:
+    """Enqueue a batch of Request structs (a list or a ctypes array); returns the ticket."""
+    if not isinstance(reqs, ctypes.Array):
+        reqs = (Request * len(reqs))(*reqs)
+    t = _u64()
+    _check(lib().prng_submit(h, ctypes.addressof(reqs), len(reqs), ctypes.byref(t), _stream(stream)))
+    return int(t.value)
+
+
+def prng_poll(h: int, ticket: int) -> bool:
+    done = _i32()
+    _check(lib().prng_poll(h, ticket, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def prng_wait(h: int, ticket: int, timeout_s: float = 60.0) -> None:
+    _check(lib().prng_wait(h, ticket, timeout_s))
+
+
+def prng_batch_get_shape(h: int) -> tuple[int, int, int]:
+    a, b, c = _i32(), _i32(), _i32()
+    _check(lib().prng_batch_get_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def prng_batch_set_shape(h: int, warps_per_block: int, blocks_per_sm: int, items_per_ticket: int) -> None:
+    _check(lib().prng_batch_set_shape(h, warps_per_block, blocks_per_sm, items_per_ticket))
 
 
 def prng_state_bytes(h: int) -> int:

@@ -17,6 +17,16 @@
 using prngd::DivConst;
 using prngd::FillParams;
 
+namespace prngd {
+// Seed streams [0, n) of `seed`.
+__global__ void seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
+  const uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const XorShift128 x = seed_stream(seed, s);
+  state[s] = make_uint4(x.x, x.y, x.z, x.w);
+}
+}  // namespace prngd
+
 namespace prngd_host {
 
 thread_local char g_err[512];
@@ -209,6 +219,7 @@ int prng_create(prng_t* out, uint64_t seed, uint64_t n_streams, int w, double a0
 int prng_destroy(prng_t h) {
   if (!h) return PRNG_OK;
   cudaDeviceSynchronize();
+  release_batch(h);
   release_aux(h);
   cudaFree(h->d_state);
   delete h;

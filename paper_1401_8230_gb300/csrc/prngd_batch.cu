@@ -1,0 +1,335 @@
+// prngd_batch.cu -- host side of the batched path: request validation, descriptor staging in
+// pinned memory, one persistent launch per batch replayed from a captured CUDA graph, tickets
+// and the launch-shape autotuner.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <numeric>
+#include <vector>
+
+#include "prngd.h"
+#include "prngd_batch.cuh"
+#include "prngd_internal.h"
+
+namespace prngd_host {
+
+static constexpr int kSlots = 4;
+
+struct BatchSlot {
+  prngd::BatchDesc* h_desc = nullptr;  // pinned
+  uint64_t* h_prefix = nullptr;        // pinned
+  uint32_t* h_nreq = nullptr;          // pinned
+  prngd::BatchDesc* d_desc = nullptr;
+  uint64_t* d_prefix = nullptr;
+  uint32_t* d_nreq = nullptr;
+  unsigned long long* d_ticket = nullptr;
+  cudaEvent_t done = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t ticket = 0;      // ticket of the batch last launched from this slot
+  int cfg_version = -1;     // launch shape the graph was captured with
+};
+
+struct BatchEngine {
+  int max_req = 0;
+  BatchSlot slot[kSlots];
+  cudaStream_t capture_stream = nullptr;
+  uint64_t next_ticket = 1;
+  int next_slot = 0;
+  BatchShape shape;
+  int cfg_version = 0;
+};
+
+void release_batch(prng_ctx* h) {
+  BatchEngine* b = h->batch;
+  if (!b) return;
+  for (auto& s : b->slot) {
+    if (s.exec) cudaGraphExecDestroy(s.exec);
+    if (s.done) cudaEventDestroy(s.done);
+    cudaFreeHost(s.h_desc);
+    cudaFreeHost(s.h_prefix);
+    cudaFreeHost(s.h_nreq);
+    cudaFree(s.d_desc);
+    cudaFree(s.d_prefix);
+    cudaFree(s.d_nreq);
+    cudaFree(s.d_ticket);
+  }
+  if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+  delete b;
+  h->batch = nullptr;
+}
+
+static int ensure_engine(prng_ctx* h) {
+  if (h->batch) return PRNG_OK;
+  BatchEngine* b = new BatchEngine();
+  b->max_req = PRNG_MAX_BATCH_REQUESTS;
+  b->shape = default_batch_shape(h->num_sms);
+  h->batch = b;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+  for (auto& s : b->slot) {
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_desc, sizeof(prngd::BatchDesc) * b->max_req);
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_prefix, sizeof(uint64_t) * (b->max_req + 1));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_nreq, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_desc, sizeof(prngd::BatchDesc) * b->max_req);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_prefix, sizeof(uint64_t) * (b->max_req + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_nreq, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_ticket, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    release_batch(h);
+    cudaGetLastError();
+    return fail(PRNG_ENOMEM, "batch engine allocation: %s", cudaGetErrorString(e));
+  }
+  return PRNG_OK;
+}
+
+BatchShape default_batch_shape(int num_sms) {
+  BatchShape s;
+  s.warps_per_block = 8;
+  s.blocks_per_sm = 4;
+  s.items_per_ticket = 1;
+  (void)num_sms;
+  return s;
+}
+
+template <int W>
+static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
+  auto k = prngd::batch_kernel<W>;
+  const size_t smem = (size_t)sh.warps_per_block * 32 * prngd::kSlotPitch;
+  const unsigned grid = (unsigned)(num_sms * sh.blocks_per_sm);
+  k<<<grid, sh.warps_per_block * 32, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, cudaStream_t s) {
+  BatchEngine* b = h->batch;
+  prngd::BatchParams p;
+  p.desc = sl.d_desc;
+  p.item_prefix = sl.d_prefix;
+  p.n_req_dev = sl.d_nreq;
+  p.ticket = sl.d_ticket;
+  p.state = h->d_state;
+  p.dc = h->dc;
+  p.scale = h->scale;
+  p.w = h->w;
+  p.one = 1;
+  p.items_per_ticket = (uint32_t)b->shape.items_per_ticket;
+  cudaError_t e = cudaMemcpyAsync(sl.d_nreq, sl.h_nreq, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(prngd::BatchDesc) * b->max_req, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, sizeof(uint64_t) * (b->max_req + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, s);
+  if (h->w == 24) return launch_batch_w<24>(p, b->shape, h->num_sms, s);
+  return launch_batch_w<0>(p, b->shape, h->num_sms, s);
+}
+
+// Capture the slot's copy + reset + launch sequence once per launch shape; replays copy the
+// pinned staging as it is at replay time.
+static int ensure_graph(prng_ctx* h, BatchSlot& sl) {
+  BatchEngine* b = h->batch;
+  if (sl.exec && sl.cfg_version == b->cfg_version) return PRNG_OK;
+  if (sl.exec) {
+    cudaGraphExecDestroy(sl.exec);
+    sl.exec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+  cudaError_t e2 = enqueue_batch(h, sl, b->capture_stream);
+  e = cudaStreamEndCapture(b->capture_stream, &g);
+  if (e2 != cudaSuccess || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(PRNG_ECUDA, "batch capture: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e));
+  }
+  e = cudaGraphInstantiate(&sl.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  sl.cfg_version = b->cfg_version;
+  return PRNG_OK;
+}
+
+// Row layout of one request (see prng_request in prngd.h).
+static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
+  if (r.form != PRNG_FORM_A_FP64 && r.form != PRNG_FORM_B_INTBITS && r.form != PRNG_FORM_C_F32PAIR)
+    return fail(PRNG_EINVAL, "request form %d", r.form);
+  if (r.length == 0) return fail(PRNG_EINVAL, "request length 0");
+  if (!r.d_out || ((uintptr_t)r.d_out & 15)) return fail(PRNG_EINVAL, "request d_out must be 16-byte aligned");
+  d.length = r.length;
+  d.out = (uint64_t*)r.d_out;
+  d.rejects = r.d_rejects;
+  d.form = r.form;
+  if (r.kind == PRNG_REQ_FRESH) {
+    const uint64_t chunk = r.chunk ? r.chunk : 1024;
+    if (chunk & 1) return fail(PRNG_EINVAL, "request chunk must be even");
+    const uint64_t rows = (r.length + chunk - 1) / chunk;
+    if (rows > 0xFFFFFFFFull) return fail(PRNG_EINVAL, "request needs too many streams");
+    d.seed = r.seed;
+    d.first_stream = r.first_stream;
+    d.per_stream = chunk;
+    d.n_rows = (uint32_t)rows;
+    d.resident = 0;
+  } else if (r.kind == PRNG_REQ_RESIDENT) {
+    if (r.n_streams == 0 || r.first_stream >= h->n_streams || r.n_streams > h->n_streams - r.first_stream)
+      return fail(PRNG_EINVAL, "resident request streams [%llu, +%llu) outside the handle's %llu streams",
+                  (unsigned long long)r.first_stream, (unsigned long long)r.n_streams,
+                  (unsigned long long)h->n_streams);
+    const uint64_t half = (r.length + 2 * r.n_streams - 1) / (2 * r.n_streams);
+    d.seed = 0;
+    d.first_stream = r.first_stream;
+    d.per_stream = 2 * half;
+    d.n_rows = (uint32_t)r.n_streams;
+    d.resident = 1;
+  } else {
+    return fail(PRNG_EINVAL, "request kind %d", r.kind);
+  }
+  d.pad = 0;
+  return PRNG_OK;
+}
+
+int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaStream_t s) {
+  if (n <= 0 || n > PRNG_MAX_BATCH_REQUESTS)
+    return fail(PRNG_EINVAL, "a batch holds 1 .. %d requests", PRNG_MAX_BATCH_REQUESTS);
+  std::vector<prngd::BatchDesc> d(n);
+  std::vector<std::pair<uint64_t, uint64_t>> ranges;
+  for (int i = 0; i < n; ++i) {
+    int rc = describe(h, reqs[i], d[i]);
+    if (rc) return rc;
+    if (d[i].resident) ranges.push_back({d[i].first_stream, d[i].first_stream + d[i].n_rows});
+  }
+  std::sort(ranges.begin(), ranges.end());
+  for (size_t i = 1; i < ranges.size(); ++i)
+    if (ranges[i].first < ranges[i - 1].second)
+      return fail(PRNG_EINVAL, "two resident requests of one batch use the same streams");
+  int rc = ensure_engine(h);
+  if (rc) return rc;
+  BatchEngine* b = h->batch;
+  // a free slot: its previous batch has finished (or it was never used)
+  BatchSlot* sl = nullptr;
+  for (int k = 0; k < kSlots && !sl; ++k) {
+    BatchSlot& c = b->slot[(b->next_slot + k) % kSlots];
+    if (c.ticket == 0 || cudaEventQuery(c.done) == cudaSuccess) {
+      sl = &c;
+      b->next_slot = (b->next_slot + k + 1) % kSlots;
+    }
+  }
+  cudaGetLastError();
+  if (!sl) return fail(PRNG_EBUSY, "all %d batch slots are in flight", kSlots);
+  // longest rows first, so the long items start early
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return d[a].per_stream > d[c].per_stream; });
+  uint64_t acc = 0;
+  for (int i = 0; i < n; ++i) {
+    sl->h_desc[i] = d[order[i]];
+    sl->h_prefix[i] = acc;
+    acc += (d[order[i]].n_rows + 31) / 32;
+  }
+  for (int i = n; i <= b->max_req; ++i) sl->h_prefix[i] = acc;
+  *sl->h_nreq = (uint32_t)n;
+  rc = ensure_graph(h, *sl);
+  if (rc) return rc;
+  cudaError_t e = cudaGraphLaunch(sl->exec, s);
+  if (e == cudaSuccess) e = cudaEventRecord(sl->done, s);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+  sl->ticket = b->next_ticket++;
+  *ticket = sl->ticket;
+  return PRNG_OK;
+}
+
+int poll(prng_ctx* h, uint64_t ticket, int* done) {
+  BatchEngine* b = h->batch;
+  if (!b || ticket == 0 || ticket >= b->next_ticket) return fail(PRNG_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+  for (auto& s : b->slot) {
+    if (s.ticket == ticket) {
+      cudaError_t e = cudaEventQuery(s.done);
+      if (e == cudaSuccess) {
+        *done = 1;
+      } else if (e == cudaErrorNotReady) {
+        *done = 0;
+        cudaGetLastError();
+      } else {
+        return fail(PRNG_ECUDA, "poll: %s", cudaGetErrorString(e));
+      }
+      return PRNG_OK;
+    }
+  }
+  *done = 1;  // the slot has been reused since, so this batch finished before
+  return PRNG_OK;
+}
+
+int set_batch_shape(prng_ctx* h, const BatchShape& sh) {
+  int rc = ensure_engine(h);
+  if (rc) return rc;
+  if (sh.warps_per_block < 1 || sh.warps_per_block > 8 || sh.blocks_per_sm < 1 || sh.blocks_per_sm > 16 ||
+      sh.items_per_ticket < 1 || sh.items_per_ticket > 64)
+    return fail(PRNG_EINVAL, "batch shape out of range");
+  for (auto& s : h->batch->slot)
+    if (s.ticket && cudaEventSynchronize(s.done) != cudaSuccess) return fail(PRNG_ECUDA, "sync before reshape");
+  h->batch->shape = sh;
+  h->batch->cfg_version++;
+  return PRNG_OK;
+}
+
+int get_batch_shape(prng_ctx* h, BatchShape* sh) {
+  int rc = ensure_engine(h);
+  if (rc) return rc;
+  *sh = h->batch->shape;
+  return PRNG_OK;
+}
+
+}  // namespace prngd_host
+
+using namespace prngd_host;
+
+extern "C" {
+
+int prng_submit(prng_t h, const prng_request* reqs, int n, uint64_t* ticket, void* cuda_stream) {
+  if (!h || !reqs || !ticket) return fail(PRNG_EINVAL, "null argument");
+  int rc = check_handle_device(h);
+  if (rc) return rc;
+  return submit(h, reqs, n, ticket, (cudaStream_t)cuda_stream);
+}
+
+int prng_poll(prng_t h, uint64_t ticket, int* done) {
+  if (!h || !done) return fail(PRNG_EINVAL, "null argument");
+  return poll(h, ticket, done);
+}
+
+int prng_wait(prng_t h, uint64_t ticket, double timeout_s) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    int done = 0;
+    int rc = poll(h, ticket, &done);
+    if (rc) return rc;
+    if (done) return PRNG_OK;
+    if (std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > timeout_s)
+      return fail(PRNG_ETIMEOUT, "ticket %llu not done after %.3f s", (unsigned long long)ticket, timeout_s);
+  }
+}
+
+int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  BatchShape sh;
+  int rc = get_batch_shape(h, &sh);
+  if (rc) return rc;
+  if (warps_per_block) *warps_per_block = sh.warps_per_block;
+  if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
+  if (items_per_ticket) *items_per_ticket = sh.items_per_ticket;
+  return PRNG_OK;
+}
+
+int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  BatchShape sh{warps_per_block, blocks_per_sm, items_per_ticket};
+  return set_batch_shape(h, sh);
+}
+
+}  // extern "C"

@@ -218,14 +218,6 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint64_t a, uint64_t
 }
 
 // ------------------------------------------------------------------------ kernels
-// Seed streams [0, n) of `seed`.
-__global__ void seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
-  const uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const XorShift128 x = seed_stream(seed, s);
-  state[s] = make_uint4(x.x, x.y, x.z, x.w);
-}
-
 // TMA path. Warp g owns streams 32g .. 32g+31 (lane = row of the tile). Per chunk of 16
 // outputs each lane computes its 16 outputs in registers, writes them as 8 x 16-byte pieces
 // into the warp's tile with the 128-byte swizzle (piece c of row r at r*128 + ((c ^ (r & 7))

@@ -4,7 +4,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "prngd.h"
 #include "prngd_math.cuh"
+
+namespace prngd_host {
+struct BatchEngine;
+struct BatchShape {
+  int warps_per_block;
+  int blocks_per_sm;
+  int items_per_ticket;
+};
+}  // namespace prngd_host
 
 struct prng_ctx {
   int device;
@@ -20,6 +30,8 @@ struct prng_ctx {
   size_t stage_bytes = 0;
   uint64_t* d_rej_stage = nullptr;
   cudaStream_t io_stream[2] = {nullptr, nullptr};
+  // batched requests (created on first use)
+  prngd_host::BatchEngine* batch = nullptr;
 };
 
 namespace prngd_host {
@@ -29,4 +41,8 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
                 uint64_t* rejects, cudaStream_t s, bool allow_tma);
 int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
 void release_aux(prng_ctx* h);
+void release_batch(prng_ctx* h);
+BatchShape default_batch_shape(int num_sms);
+int set_batch_shape(prng_ctx* h, const BatchShape& sh);
+int get_batch_shape(prng_ctx* h, BatchShape* sh);
 }  // namespace prngd_host

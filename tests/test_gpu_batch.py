@@ -1,0 +1,196 @@
+"""GPU parity of the batched path (prng_submit / prng_poll / prng_wait) against the oracle.
+
+A fresh request's output is streams first_stream .. of its seed, `chunk` outputs each,
+concatenated and cut at `length`; a resident request continues the handle's streams with
+rows of per = 2 ceil(L / 2n) outputs. Values, reject counts and the resident state advance
+must be identical to the oracle, whatever the batch, its other requests or the launch shape."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1401_8230_gb300 as P  # noqa: E402
+from paper_1401_8230_gb300 import workloads  # noqa: E402
+
+OF = {P.FORM_A_FP64: O.FORM_A, P.FORM_B_INTBITS: O.FORM_B, P.FORM_C_F32PAIR: O.FORM_C}
+
+
+def oracle_fresh(seed, first, length, chunk, w, form):
+    """Expected output and per-row reject counts of a fresh request."""
+    chunk = chunk or 1024
+    rows = (length + chunk - 1) // chunk
+    vals, rej = [], []
+    full = rows - 1
+    if full:
+        v, r = O.fill(seed, first, full, chunk, w, OF[form])
+        vals.append(v)
+        rej.append(r)
+    last = length - full * chunk
+    v, r = O.fill(seed, first + full, 1, last, w, OF[form])
+    vals.append(v)
+    rej.append(r)
+    return np.concatenate(vals), np.concatenate(rej)
+
+
+def oracle_resident(states, length, w, form):
+    """Expected output, rejects and new states of a resident request over `states`."""
+    n = len(states)
+    per = 2 * ((length + 2 * n - 1) // (2 * n))
+    vals, rej, new = [], [], []
+    for j, st in enumerate(states):
+        cnt = max(0, min(per, length - j * per))
+        v, r, s2 = O.fill_state(st, cnt, w, OF[form])
+        vals.append(v)
+        rej.append(r)
+        new.append(s2)
+    return np.concatenate(vals), np.array(rej, dtype=np.uint64), new
+
+
+def dev_buf(length):
+    return torch.zeros(length + 2, dtype=torch.float64, device="cuda")  # 256-byte aligned base
+
+
+def as_host(buf, length, form):
+    a = buf[:length].cpu().numpy()
+    return a.view(np.float32) if form == P.FORM_C_F32PAIR else a
+
+
+def same(a, b):
+    return np.array_equal(np.ascontiguousarray(a).view(np.uint8), np.ascontiguousarray(b).view(np.uint8))
+
+
+@pytest.mark.parametrize("w", [32, 24, 8])
+def test_fresh_requests_match_the_oracle(w):
+    rng = np.random.default_rng(w)
+    cases = [(1, 0), (15, 0), (16, 0), (17, 1024), (1023, 0), (1024, 0), (1025, 0), (5000, 64), (777, 6),
+             (3, 2), (40000, 1000)]
+    with P.Generator(3, 1, w) as g:
+        reqs, bufs, want = [], [], []
+        for i, (L, chunk) in enumerate(cases):
+            form = [P.FORM_B_INTBITS, P.FORM_A_FP64, P.FORM_C_F32PAIR][i % 3]
+            seed = int(rng.integers(0, 2**63))
+            first = int(rng.integers(0, 2**20))
+            b = dev_buf(L)
+            rej = torch.full(((L + (chunk or 1024) - 1) // (chunk or 1024),), 9, dtype=torch.int64, device="cuda")
+            reqs.append(P.fresh_request(b, L, seed, first, form, chunk, rej))
+            bufs.append((b, rej, L, form))
+            want.append(oracle_fresh(seed, first, L, chunk, w, form))
+        t = P.prng_submit(g.h, reqs)
+        P.prng_wait(g.h, t, 60)
+        assert P.prng_poll(g.h, t)
+        for (b, rej, L, form), (wv, wr) in zip(bufs, want):
+            assert same(as_host(b, L, form), wv), (L, form)
+            assert np.array_equal(rej.cpu().numpy().astype(np.uint64), wr)
+            assert b[L:].abs().sum().item() == 0  # nothing written past the request
+
+
+@pytest.mark.parametrize("w", [32, 24])
+def test_resident_requests_continue_streams(w):
+    seed, ns = 11, 300
+    with P.Generator(seed, ns, w) as g:
+        states = [O.stream_seed(seed, s) for s in range(ns)]
+        # two batches: [0,100) and [100,300) in the first, [0,300) in the second
+        plan = [[(0, 100, 1001, P.FORM_B_INTBITS), (100, 200, 64, P.FORM_C_F32PAIR)],
+                [(0, 300, 99999, P.FORM_A_FP64)]]
+        for batch in plan:
+            reqs, bufs = [], []
+            for first, n, L, form in batch:
+                b = dev_buf(L)
+                rej = torch.zeros(n, dtype=torch.int64, device="cuda")
+                reqs.append(P.resident_request(b, L, first, n, form, rej))
+                bufs.append((b, rej, first, n, L, form))
+            t = P.prng_submit(g.h, reqs)
+            P.prng_wait(g.h, t, 60)
+            for b, rej, first, n, L, form in bufs:
+                wv, wr, new = oracle_resident(states[first:first + n], L, w, form)
+                assert same(as_host(b, L, form), wv)
+                assert np.array_equal(rej.cpu().numpy().astype(np.uint64), wr)
+                states[first:first + n] = new
+        # the device state equals the oracle's after both batches
+        st = np.zeros(P.prng_state_bytes(g.h), dtype=np.uint8)
+        g.state_save(st)
+        assert np.array_equal(st.view(np.uint32).reshape(ns, 4), np.array(states))
+
+
+def test_result_is_the_same_alone_and_in_a_mix_and_for_any_launch_shape():
+    seed = 5
+    with P.Generator(seed, 4096, 32) as g:
+        target = dict(L=30011, seed=77, first=123, form=P.FORM_B_INTBITS)
+
+        def run_target(extra, shape):
+            P.prng_batch_set_shape(g.h, *shape)
+            reqs, keep = [], []
+            b = dev_buf(target["L"])
+            reqs.append(P.fresh_request(b, target["L"], target["seed"], target["first"], target["form"]))
+            for i in range(extra):
+                e = dev_buf(1000 + 37 * i)
+                keep.append(e)
+                reqs.append(P.fresh_request(e, 1000 + 37 * i, 1000 + i, i, (i % 3)))
+            P.prng_wait(g.h, P.prng_submit(g.h, reqs), 60)
+            return as_host(b, target["L"], target["form"])
+
+        alone = run_target(0, (8, 4, 1))
+        mixed = run_target(200, (8, 4, 1))
+        other = run_target(200, (1, 1, 5))
+        want, _ = oracle_fresh(77, 123, 30011, 0, 32, P.FORM_B_INTBITS)
+        assert same(alone, want) and same(mixed, want) and same(other, want)
+        P.prng_batch_set_shape(g.h, 8, 4, 1)
+
+
+def test_batch_errors():
+    with P.Generator(1, 64, 32) as g:
+        b = dev_buf(100)
+        with pytest.raises(P.PrngError) as e:  # overlapping resident ranges
+            P.prng_submit(g.h, [P.resident_request(b, 10, 0, 10), P.resident_request(b, 10, 5, 10)])
+        assert e.value.code == P.PRNG_EINVAL
+        with pytest.raises(P.PrngError) as e:  # outside the handle
+            P.prng_submit(g.h, [P.resident_request(b, 10, 60, 10)])
+        assert e.value.code == P.PRNG_EINVAL
+        with pytest.raises(P.PrngError) as e:  # 8-byte (not 16-byte) aligned output
+            P.prng_submit(g.h, [P.fresh_request(b[1:], 10, 1, 0)])
+        assert e.value.code == P.PRNG_EINVAL
+        with pytest.raises(P.PrngError) as e:  # odd chunk
+            P.prng_submit(g.h, [P.fresh_request(b, 10, 1, 0, 1, 3)])
+        assert e.value.code == P.PRNG_EINVAL
+        with pytest.raises(P.PrngError) as e:
+            P.prng_poll(g.h, 12345)
+        assert e.value.code == P.PRNG_ENOTFOUND
+        # more batches than slots in flight: EBUSY, then fine after waiting
+        big = torch.empty(2**24, dtype=torch.float64, device="cuda")
+        tickets, busy = [], False
+        for k in range(12):
+            try:
+                tickets.append(P.prng_submit(g.h, [P.fresh_request(big, 2**24, k, 0)]))
+            except P.PrngError as err:
+                assert err.code == P.PRNG_EBUSY
+                busy = True
+                break
+        for t in tickets:
+            P.prng_wait(g.h, t, 60)
+        assert busy or len(tickets) == 12
+        P.prng_wait(g.h, P.prng_submit(g.h, [P.fresh_request(b, 10, 1, 0)]), 60)
+
+
+def test_batched_workload_sampled():
+    """The batched workload at reduced size: 512 requests, log-uniform lengths in [2^8, 2^20],
+    own seeds and stream offsets, one launch; 24 requests compared output by output."""
+    spec = workloads.batched_requests(n=512, lo=2**8, hi=2**20, seed=1)
+    with P.Generator(1, 1, 32) as g:
+        total = sum(r["length"] for r in spec)
+        pool = torch.empty(total + 2 * len(spec), dtype=torch.float64, device="cuda")
+        reqs, offs, off = [], [], 0
+        for r in spec:
+            offs.append(off)
+            reqs.append(P.fresh_request(pool[off:], r["length"], r["seed"], r["first_stream"], P.FORM_B_INTBITS))
+            off += (r["length"] + 1) // 2 * 2
+        P.prng_wait(g.h, P.prng_submit(g.h, reqs), 120)
+        rng = np.random.default_rng(2)
+        pick = rng.choice(len(spec), 24, replace=False)
+        for i in pick:
+            r = spec[i]
+            got = pool[offs[i]:offs[i] + r["length"]].cpu().numpy()
+            want, _ = oracle_fresh(r["seed"], r["first_stream"], r["length"], 1024, 32, P.FORM_B_INTBITS)
+            assert same(got, want), i
