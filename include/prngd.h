@@ -219,6 +219,61 @@ int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int
 int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket);
 
 /*
+ * Serving loop. A server keeps per-client generator state resident on the device and runs
+ * client fill requests with continuous batching. The paper has no serving layer; each
+ * request is the method of Section 2 applied to the client's streams.
+ *
+ * Clients: client c owns the handle's streams [c S, (c+1) S) (S = streams_per_client, which
+ * must divide the handle's stream count). A request of `length` outputs from client c is the
+ * resident request (see prng_request) over the first n = min(S, ceil(length /
+ * min_per_stream)) of the client's streams. A client's requests run one at a time in
+ * admission order, so a result is fixed by the client's history and the request alone,
+ * never by what else is in flight.
+ *
+ * Admission: prng_server_submit takes output memory from a device pool of pool_bytes
+ * (allocated once by prng_server_create) and returns PRNG_EBUSY when it does not fit;
+ * the caller retries after releasing finished requests.
+ * Batching: prng_server_step harvests finished batches and launches every admitted request
+ * whose client is idle as one batch (small and large requests on two CUDA streams), so work
+ * admitted while other batches run overlaps with them on the device.
+ * Results stay in the pool until prng_server_release; prng_server_poll gives the device
+ * pointer, prng_server_read copies them to the host.
+ * A server is not thread-safe. Errors as for the batch calls; PRNG_ENOTFOUND for an unknown
+ * request id.
+ */
+typedef struct prng_server* prng_server_t;
+
+int prng_server_create(prng_server_t* out, prng_t h, uint64_t streams_per_client,
+                       uint64_t min_per_stream, size_t pool_bytes);
+int prng_server_destroy(prng_server_t s);
+int prng_server_submit(prng_server_t s, uint64_t client, uint64_t length, int form, uint64_t* id);
+int prng_server_step(prng_server_t s);
+int prng_server_poll(prng_server_t s, uint64_t id, int* done, void** d_out);
+int prng_server_read(prng_server_t s, uint64_t id, void* host_dst, size_t bytes);
+int prng_server_release(prng_server_t s, uint64_t id);
+/* Step until nothing is waiting or running, at most timeout_s seconds (PRNG_ETIMEOUT). */
+int prng_server_drain(prng_server_t s, double timeout_s);
+int prng_server_info(prng_server_t s, uint64_t* n_clients, uint64_t* batches, uint64_t* completed,
+                     uint64_t* samples, size_t* pool_used);
+
+/*
+ * prng_server_run_trace -- replay an arrival trace in real time: item i arrives t seconds
+ * after the call starts (items sorted by t), is admitted in arrival order when the pool has
+ * room, runs, and is released as soon as it finishes. latency (nullable, n doubles) gets
+ * finish time minus arrival time per item; makespan (nullable) the total wall time.
+ * Errors: PRNG_ETIMEOUT after timeout_s seconds, and those of the calls above.
+ */
+typedef struct prng_trace_item {
+  double t;         /* arrival time, seconds from the start of the replay */
+  uint64_t client;
+  uint64_t length;  /* outputs */
+  int32_t form;
+  int32_t reserved;
+} prng_trace_item;
+int prng_server_run_trace(prng_server_t s, const prng_trace_item* items, uint64_t n, double* latency,
+                          double* makespan, double timeout_s);
+
+/*
  * State checkpoint: each stream's state is 16 bytes (xorshift128 words x, y, z, w).
  * prng_state_bytes gives n_streams * 16. save copies the device state into host_buf and
  * restore copies it back; both synchronise. A fill after restore reproduces the outputs

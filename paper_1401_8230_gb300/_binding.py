@@ -13,6 +13,12 @@ REQ_FRESH, REQ_RESIDENT = 0, 1
 MAX_BATCH_REQUESTS = 4096
 
 
+class TraceItem(ctypes.Structure):
+    """struct prng_trace_item of include/prngd.h."""
+    _fields_ = [("t", ctypes.c_double), ("client", ctypes.c_uint64), ("length", ctypes.c_uint64),
+                ("form", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Request(ctypes.Structure):
     """struct prng_request of include/prngd.h."""
     _fields_ = [("kind", ctypes.c_int32), ("form", ctypes.c_int32), ("length", ctypes.c_uint64),
@@ -52,6 +58,17 @@ _SIGNATURES = {
     "prng_wait": (_i32, [_P, _u64, _dbl]),
     "prng_batch_get_shape": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "prng_batch_set_shape": (_i32, [_P, _i32, _i32, _i32]),
+    "prng_server_create": (_i32, [ctypes.POINTER(_P), _P, _u64, _u64, _sz]),
+    "prng_server_destroy": (_i32, [_P]),
+    "prng_server_submit": (_i32, [_P, _u64, _u64, _i32, ctypes.POINTER(_u64)]),
+    "prng_server_step": (_i32, [_P]),
+    "prng_server_poll": (_i32, [_P, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_vp)]),
+    "prng_server_read": (_i32, [_P, _u64, _vp, _sz]),
+    "prng_server_release": (_i32, [_P, _u64]),
+    "prng_server_drain": (_i32, [_P, _dbl]),
+    "prng_server_info": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
+                                ctypes.POINTER(_u64), ctypes.POINTER(_sz)]),
+    "prng_server_run_trace": (_i32, [_P, _vp, _u64, _vp, ctypes.POINTER(_dbl), _dbl]),
     "prng_state_save": (_i32, [_P, _vp, _sz]),
     "prng_state_restore": (_i32, [_P, _vp, _sz]),
 }
@@ -188,6 +205,63 @@ def prng_batch_get_shape(h: int) -> tuple[int, int, int]:
 
 def prng_batch_set_shape(h: int, warps_per_block: int, blocks_per_sm: int, items_per_ticket: int) -> None:
     _check(lib().prng_batch_set_shape(h, warps_per_block, blocks_per_sm, items_per_ticket))
+
+
+def prng_server_create(h: int, streams_per_client: int, min_per_stream: int = 256, pool_bytes: int = 32 << 30) -> int:
+    s = _P()
+    _check(lib().prng_server_create(ctypes.byref(s), h, streams_per_client, min_per_stream, pool_bytes))
+    return s.value
+
+
+def prng_server_destroy(s: int) -> None:
+    _check(lib().prng_server_destroy(s))
+
+
+def prng_server_submit(s: int, client: int, length: int, form: int = FORM_B_INTBITS) -> int:
+    i = _u64()
+    _check(lib().prng_server_submit(s, client, length, form, ctypes.byref(i)))
+    return int(i.value)
+
+
+def prng_server_step(s: int) -> None:
+    _check(lib().prng_server_step(s))
+
+
+def prng_server_poll(s: int, rid: int) -> tuple[bool, int]:
+    done, ptr = _i32(), _vp()
+    _check(lib().prng_server_poll(s, rid, ctypes.byref(done), ctypes.byref(ptr)))
+    return bool(done.value), int(ptr.value or 0)
+
+
+def prng_server_read(s: int, rid: int, host) -> None:
+    _check(lib().prng_server_read(s, rid, _ptr(host), host.nbytes))
+
+
+def prng_server_release(s: int, rid: int) -> None:
+    _check(lib().prng_server_release(s, rid))
+
+
+def prng_server_drain(s: int, timeout_s: float = 60.0) -> None:
+    _check(lib().prng_server_drain(s, timeout_s))
+
+
+def prng_server_info(s: int) -> dict:
+    a, b, c, d, e = _u64(), _u64(), _u64(), _u64(), _sz()
+    _check(lib().prng_server_info(s, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d),
+                                  ctypes.byref(e)))
+    return {"clients": a.value, "batches": b.value, "completed": c.value, "samples": d.value, "pool_used": e.value}
+
+
+def prng_server_run_trace(s: int, items, timeout_s: float = 600.0):
+    """Replay [(t, client, length, form), ...] in real time; returns (latencies, makespan)."""
+    import numpy as np
+
+    arr = (TraceItem * len(items))(*[TraceItem(float(t), int(c), int(L), int(f), 0) for t, c, L, f in items])
+    lat = np.zeros(len(items), dtype=np.float64)
+    mk = _dbl()
+    _check(lib().prng_server_run_trace(s, ctypes.addressof(arr), len(items), lat.ctypes.data, ctypes.byref(mk),
+                                       timeout_s))
+    return lat, mk.value
 
 
 def prng_state_bytes(h: int) -> int:

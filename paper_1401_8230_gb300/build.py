@@ -20,7 +20,7 @@ LIB_DIR = os.path.join(HERE, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libprngd.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
-SOURCES = ["prngd.cu", "prngd_io.cu", "prngd_stats.cu", "prngd_noalloc.cu", "prngd_batch.cu"]
+SOURCES = ["prngd.cu", "prngd_io.cu", "prngd_stats.cu", "prngd_noalloc.cu", "prngd_batch.cu", "prngd_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -46,7 +46,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OBJ_DIR, os.path.splitext(src)[0] + ".o")
+        obj = os.path.join(OBJ_DIR, os.path.splitext(src)[0] + ".o")  # .cpp: host-only, same flags
         cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)

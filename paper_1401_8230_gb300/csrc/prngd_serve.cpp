@@ -1,0 +1,373 @@
+// prngd_serve.cpp -- the serving loop: admission of fill requests against an output-pool
+// budget, continuous batching onto the device, per-client resident streams, latency stats.
+//
+// Clients: client c owns the handle's streams [c S, (c+1) S). A request of length L from c
+// continues the first n = min(S, ceil(L / min_per_stream)) of them as one resident request
+// (rows of 2 ceil(L / 2n) outputs), so a request's result is fixed by the client's history
+// and the request itself, never by what else is in flight. A client has at most one request
+// on the device at a time; later requests of a busy client wait in order.
+//
+// Batching: step() puts every admitted request whose client is idle into the next batch
+// (small and large requests go to two separate CUDA streams, so small requests do not wait
+// behind large ones) and harvests finished batches. Requests that arrive while batches run
+// are admitted as soon as pool memory allows and join the next batch; batches overlap on
+// the device.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "prngd.h"
+#include "prngd_internal.h"
+
+using prngd_host::fail;
+
+namespace {
+
+// First-fit allocator over one device allocation (offsets in bytes, 256-byte granules).
+class Pool {
+ public:
+  bool init(size_t bytes) {
+    if (cudaMalloc(&base_, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    size_ = bytes;
+    free_[0] = bytes;
+    return true;
+  }
+  ~Pool() {
+    if (base_) cudaFree(base_);
+  }
+  // returns offset or SIZE_MAX
+  size_t alloc(size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        const size_t off = it->first, len = it->second;
+        free_.erase(it);
+        if (len > bytes) free_[off + bytes] = len - bytes;
+        used_ += bytes;
+        return off;
+      }
+    }
+    return SIZE_MAX;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  void* ptr(size_t off) const { return (char*)base_ + off; }
+  size_t used() const { return used_; }
+  size_t size() const { return size_; }
+
+ private:
+  void* base_ = nullptr;
+  size_t size_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+struct Req {
+  uint64_t client, length;
+  int form;
+  size_t off, bytes;
+  int state;  // 0 admitted, 1 launched, 2 done
+  uint64_t ticket;
+  double t_admit, t_done;
+};
+
+constexpr int kLanes = 2;                      // small / large requests
+constexpr uint64_t kLargeOutputs = 1ull << 20;  // requests above this go to the large lane
+
+}  // namespace
+
+struct prng_server {
+  prng_t h = nullptr;
+  uint64_t S = 0, min_per = 0, n_clients = 0;
+  Pool pool;
+  cudaStream_t lane_stream[kLanes] = {nullptr, nullptr};
+  uint64_t next_id = 1;
+  std::unordered_map<uint64_t, Req> reqs;
+  std::deque<uint64_t> waiting[kLanes];              // admitted, not launched (arrival order)
+  std::unordered_map<uint64_t, uint64_t> busy;       // client -> id on the device
+  std::unordered_map<uint64_t, std::deque<uint64_t>> client_q;  // admitted, not launched, per client
+  std::vector<std::pair<uint64_t, std::vector<uint64_t>>> inflight;  // ticket -> ids
+  uint64_t launched_batches = 0, completed = 0, samples_done = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+namespace {
+
+int harvest(prng_server* s) {
+  for (size_t k = 0; k < s->inflight.size();) {
+    int done = 0;
+    int rc = prng_poll(s->h, s->inflight[k].first, &done);
+    if (rc) return rc;
+    if (!done) {
+      ++k;
+      continue;
+    }
+    const double t = s->now();
+    for (uint64_t id : s->inflight[k].second) {
+      Req& r = s->reqs[id];
+      r.state = 2;
+      r.t_done = t;
+      s->busy.erase(r.client);
+      s->completed++;
+      s->samples_done += r.length;
+    }
+    s->inflight.erase(s->inflight.begin() + k);
+  }
+  return PRNG_OK;
+}
+
+int launch_lane(prng_server* s, int lane) {
+  std::vector<prng_request> batch;
+  std::vector<uint64_t> ids;
+  std::deque<uint64_t> keep;
+  std::unordered_map<uint64_t, bool> taken;  // one request per client per batch
+  while (!s->waiting[lane].empty()) {
+    const uint64_t id = s->waiting[lane].front();
+    s->waiting[lane].pop_front();
+    Req& r = s->reqs[id];
+    // a client's requests run one at a time, in admission order
+    if (s->busy.count(r.client) || taken.count(r.client) || s->client_q[r.client].front() != id ||
+        (int)batch.size() >= PRNG_MAX_BATCH_REQUESTS) {
+      keep.push_back(id);
+      continue;
+    }
+    taken[r.client] = true;
+    const uint64_t n = std::min<uint64_t>(s->S, (r.length + s->min_per - 1) / s->min_per);
+    prng_request q{};
+    q.kind = PRNG_REQ_RESIDENT;
+    q.form = r.form;
+    q.length = r.length;
+    q.first_stream = r.client * s->S;
+    q.n_streams = n;
+    q.d_out = s->pool.ptr(r.off);
+    batch.push_back(q);
+    ids.push_back(id);
+  }
+  s->waiting[lane] = std::move(keep);
+  if (batch.empty()) return PRNG_OK;
+  uint64_t ticket = 0;
+  int rc = prng_submit(s->h, batch.data(), (int)batch.size(), &ticket, s->lane_stream[lane]);
+  if (rc == PRNG_EBUSY) {  // no free batch slot: put them back in front, in order
+    for (size_t i = ids.size(); i-- > 0;) s->waiting[lane].push_front(ids[i]);
+    return PRNG_OK;
+  }
+  if (rc) return rc;
+  for (uint64_t id : ids) {
+    Req& r = s->reqs[id];
+    r.state = 1;
+    r.ticket = ticket;
+    s->busy[r.client] = id;
+    auto& q = s->client_q[r.client];
+    q.pop_front();
+    if (q.empty()) s->client_q.erase(r.client);
+  }
+  s->inflight.push_back({ticket, ids});
+  s->launched_batches++;
+  return PRNG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prng_server_create(prng_server_t* out, prng_t h, uint64_t streams_per_client, uint64_t min_per_stream,
+                       size_t pool_bytes) {
+  if (!out || !h) return fail(PRNG_EINVAL, "null argument");
+  *out = nullptr;
+  uint64_t n_streams = 0;
+  int w = 0;
+  int rc = prng_get_info(h, &n_streams, &w);
+  if (rc) return rc;
+  if (streams_per_client == 0 || streams_per_client > n_streams || n_streams % streams_per_client)
+    return fail(PRNG_EINVAL, "streams_per_client must divide the handle's %llu streams", (unsigned long long)n_streams);
+  if (min_per_stream == 0) min_per_stream = 256;
+  if (pool_bytes < 4096) return fail(PRNG_EINVAL, "pool too small");
+  prng_server* s = new prng_server();
+  s->h = h;
+  s->S = streams_per_client;
+  s->min_per = min_per_stream;
+  s->n_clients = n_streams / streams_per_client;
+  if (!s->pool.init(pool_bytes)) {
+    delete s;
+    return fail(PRNG_ENOMEM, "output pool of %zu bytes", pool_bytes);
+  }
+  for (int l = 0; l < kLanes; ++l)
+    if (cudaStreamCreateWithFlags(&s->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess) {
+      for (int k = 0; k < l; ++k) cudaStreamDestroy(s->lane_stream[k]);
+      delete s;
+      return fail(PRNG_ECUDA, "stream creation");
+    }
+  *out = s;
+  return PRNG_OK;
+}
+
+int prng_server_destroy(prng_server_t s) {
+  if (!s) return PRNG_OK;
+  for (int l = 0; l < kLanes; ++l) {
+    cudaStreamSynchronize(s->lane_stream[l]);
+    cudaStreamDestroy(s->lane_stream[l]);
+  }
+  delete s;
+  return PRNG_OK;
+}
+
+int prng_server_submit(prng_server_t s, uint64_t client, uint64_t length, int form, uint64_t* id) {
+  if (!s || !id) return fail(PRNG_EINVAL, "null argument");
+  if (client >= s->n_clients) return fail(PRNG_EINVAL, "client %llu of %llu", (unsigned long long)client,
+                                          (unsigned long long)s->n_clients);
+  if (length == 0) return fail(PRNG_EINVAL, "length 0");
+  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR)
+    return fail(PRNG_EINVAL, "form %d", form);
+  const size_t bytes = (size_t)length * 8;
+  if (bytes > s->pool.size()) return fail(PRNG_EINVAL, "request larger than the whole pool");
+  const size_t off = s->pool.alloc(bytes);
+  if (off == SIZE_MAX) return fail(PRNG_EBUSY, "output pool full (%zu of %zu bytes in use)", s->pool.used(), s->pool.size());
+  Req r;
+  r.client = client;
+  r.length = length;
+  r.form = form;
+  r.off = off;
+  r.bytes = bytes;
+  r.state = 0;
+  r.ticket = 0;
+  r.t_admit = s->now();
+  r.t_done = 0;
+  *id = s->next_id++;
+  s->reqs[*id] = r;
+  s->waiting[length > kLargeOutputs ? 1 : 0].push_back(*id);
+  s->client_q[client].push_back(*id);
+  return PRNG_OK;
+}
+
+int prng_server_step(prng_server_t s) {
+  if (!s) return fail(PRNG_EINVAL, "null server");
+  int rc = harvest(s);
+  if (rc) return rc;
+  for (int l = 0; l < kLanes; ++l) {
+    rc = launch_lane(s, l);
+    if (rc) return rc;
+  }
+  return PRNG_OK;
+}
+
+int prng_server_poll(prng_server_t s, uint64_t id, int* done, void** d_out) {
+  if (!s || !done) return fail(PRNG_EINVAL, "null argument");
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(PRNG_ENOTFOUND, "request %llu", (unsigned long long)id);
+  *done = it->second.state == 2;
+  if (d_out) *d_out = s->pool.ptr(it->second.off);
+  return PRNG_OK;
+}
+
+int prng_server_read(prng_server_t s, uint64_t id, void* host_dst, size_t bytes) {
+  if (!s || !host_dst) return fail(PRNG_EINVAL, "null argument");
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(PRNG_ENOTFOUND, "request %llu", (unsigned long long)id);
+  if (it->second.state != 2) return fail(PRNG_EBUSY, "request %llu has not finished", (unsigned long long)id);
+  if (bytes != it->second.bytes) return fail(PRNG_EINVAL, "bytes must be 8 * length");
+  cudaError_t e = cudaMemcpy(host_dst, s->pool.ptr(it->second.off), bytes, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "read: %s", cudaGetErrorString(e));
+  return PRNG_OK;
+}
+
+int prng_server_release(prng_server_t s, uint64_t id) {
+  if (!s) return fail(PRNG_EINVAL, "null server");
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(PRNG_ENOTFOUND, "request %llu", (unsigned long long)id);
+  if (it->second.state != 2) return fail(PRNG_EBUSY, "request %llu has not finished", (unsigned long long)id);
+  s->pool.release(it->second.off, it->second.bytes);
+  s->reqs.erase(it);
+  return PRNG_OK;
+}
+
+int prng_server_drain(prng_server_t s, double timeout_s) {
+  if (!s) return fail(PRNG_EINVAL, "null server");
+  const double t_end = s->now() + timeout_s;
+  for (;;) {
+    int rc = prng_server_step(s);
+    if (rc) return rc;
+    bool idle = s->inflight.empty();
+    for (int l = 0; l < kLanes; ++l) idle = idle && s->waiting[l].empty();
+    if (idle) return PRNG_OK;
+    if (s->now() > t_end) return fail(PRNG_ETIMEOUT, "server not drained after %.3f s", timeout_s);
+  }
+}
+
+int prng_server_run_trace(prng_server_t s, const prng_trace_item* items, uint64_t n, double* latency,
+                          double* makespan, double timeout_s) {
+  if (!s || (!items && n)) return fail(PRNG_EINVAL, "null argument");
+  const double t_start = s->now();
+  std::deque<uint64_t> arrived;              // indices waiting for pool memory
+  std::vector<uint64_t> ids(n, 0);
+  std::unordered_map<uint64_t, uint64_t> id_to_index;
+  uint64_t next = 0, finished = 0;
+  while (finished < n) {
+    const double t = s->now() - t_start;
+    if (t > timeout_s) return fail(PRNG_ETIMEOUT, "trace not finished after %.1f s (%llu of %llu done)", timeout_s,
+                                   (unsigned long long)finished, (unsigned long long)n);
+    while (next < n && items[next].t <= t) arrived.push_back(next++);
+    while (!arrived.empty()) {  // admission in arrival order
+      const uint64_t i = arrived.front();
+      uint64_t id = 0;
+      int rc = prng_server_submit(s, items[i].client, items[i].length, items[i].form, &id);
+      if (rc == PRNG_EBUSY) break;
+      if (rc) return rc;
+      ids[i] = id;
+      id_to_index[id] = i;
+      arrived.pop_front();
+    }
+    int rc = prng_server_step(s);
+    if (rc) return rc;
+    // completions: record latency from arrival, release the output
+    for (auto it = id_to_index.begin(); it != id_to_index.end();) {
+      Req& r = s->reqs[it->first];
+      if (r.state == 2) {
+        if (latency) latency[it->second] = (r.t_done - t_start) - items[it->second].t;
+        prng_server_release(s, it->first);
+        it = id_to_index.erase(it);
+        ++finished;
+      } else {
+        ++it;
+      }
+    }
+  }
+  if (makespan) *makespan = s->now() - t_start;
+  return PRNG_OK;
+}
+
+int prng_server_info(prng_server_t s, uint64_t* n_clients, uint64_t* batches, uint64_t* completed,
+                     uint64_t* samples, size_t* pool_used) {
+  if (!s) return fail(PRNG_EINVAL, "null server");
+  if (n_clients) *n_clients = s->n_clients;
+  if (batches) *batches = s->launched_batches;
+  if (completed) *completed = s->completed;
+  if (samples) *samples = s->samples_done;
+  if (pool_used) *pool_used = s->pool.used();
+  return PRNG_OK;
+}
+
+}  // extern "C"
