@@ -217,6 +217,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--n-streams", type=int, default=None, help="override the stream count (profiling runs)")
     ap.add_argument("--per-stream", type=int, default=None, help="override outputs per stream (profiling runs)")
     args = ap.parse_args()
@@ -295,10 +298,18 @@ def main():
 
     if rank == 0 and not args.no_extras:
         line["forms"] = extras(torch, P, g, out, stream, peak)
+    plain_rate = value / world
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(torch, P, g, samples_step)
     del out
     g.close()
+    if rank == 0 and not args.no_batched:
+        torch.cuda.empty_cache()
+        line["batched"] = batched(torch, P, stream, plain_rate)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_served:
+        line["served"] = served(torch, P, plain_rate, args.serve_seconds)
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -346,6 +357,97 @@ def extras(torch, P, g, out, stream, peak):
     return res
 
 
+TUNE_TABLE = os.path.join(ROOT, "paper_1401_8230_gb300", "lib", "autotune.txt")
+
+
+def batched(torch, P, stream, plain_rate):
+    """4096 fresh requests, log-uniform lengths in [2^8, 2^26], own seeds and stream offsets,
+    w = 32 form B, one persistent launch (graph replay) with the autotuned shape; against the
+    same requests as 4096 single-request launches."""
+    from paper_1401_8230_gb300 import workloads
+
+    spec = workloads.batched_requests(n=4096, lo=2**8, hi=2**26, seed=1)
+    sizes = [(r["length"] + 1) // 2 * 2 for r in spec]
+    total = sum(r["length"] for r in spec)
+    g = P.Generator(SEED, 1, W)
+    pool = torch.empty(sum(sizes) + 2, dtype=torch.float64, device="cuda")
+    reqs, off = [], 0
+    for r, sz in zip(spec, sizes):
+        reqs.append(P.fresh_request(pool[off:], r["length"], r["seed"], r["first_stream"], P.FORM_B_INTBITS))
+        off += sz
+    tuned = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, 2**26, TUNE_TABLE)
+    import ctypes
+
+    arr = (P.Request * len(reqs))(*reqs)
+
+    def one_batch():
+        P.prng_submit(g.h, arr, stream)
+
+    one_batch()
+    times = time_calls(torch, one_batch, 3, stream)
+    ms = sorted(times)[1]
+    # plain: one launch per request on the same stream
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    for k in range(2):
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for q in reqs:
+            while True:
+                try:
+                    P.prng_submit(g.h, [q], stream)
+                    break
+                except P.PrngError as e:
+                    if e.code != P.PRNG_EBUSY:
+                        raise
+        t1.record(stream)
+        torch.cuda.synchronize()
+    plain_ms = t0.elapsed_time(t1)
+    del pool
+    g.close()
+    rate = total / (ms * 1e-3) / 1e9
+    return {"requests": len(spec), "outputs": total, "gsamples_s": rate, "ms": ms,
+            "vs_plain_fill": rate / plain_rate, "per_request_launches_gsamples_s": total / (plain_ms * 1e-3) / 1e9,
+            "per_request_launches_ms": plain_ms, "shape": tuned, "graph": True}
+
+
+def served(torch, P, plain_rate, seconds):
+    """Poisson arrivals at 20k requests/s for `seconds`, lengths log-uniform in [2^10, 2^28],
+    form uniform over A/B/C, 2^16 clients with 16384 resident streams each (16 GiB of state),
+    32 GiB output pool; requests replayed in real time by the library's serving loop. Then the
+    same server at saturation (all of a fixed request set arriving at once)."""
+    import numpy as np
+
+    from paper_1401_8230_gb300 import workloads
+
+    clients, S = 2**16, 16384
+    g = P.Generator(SEED, clients * S, W)
+    srv = P.prng_server_create(g.h, S, 1024, 32 << 30)
+    try:
+        P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**10, 2**28, TUNE_TABLE)
+        trace = workloads.serving_arrivals(seconds, 20000.0, 2**10, 2**28, clients, seed=1)
+        items = [(r["t"], r["client"], r["length"], r["form"]) for r in trace]
+        lat, makespan = P.prng_server_run_trace(srv, items, 600)
+        total = sum(r["length"] for r in trace)
+        info = P.prng_server_info(srv)
+        sat = workloads.serving_arrivals(1.0, 4000.0, 2**10, 2**28, clients, seed=2)
+        sat_items = [(0.0, r["client"], r["length"], r["form"]) for r in sat]
+        _, sat_makespan = P.prng_server_run_trace(srv, sat_items, 600)
+        sat_total = sum(r["length"] for r in sat)
+    finally:
+        P.prng_server_destroy(srv)
+        g.close()
+    rate = total / makespan / 1e9
+    sat_rate = sat_total / sat_makespan / 1e9
+    return {"requests": len(trace), "outputs": total, "offered_gsamples_s": total / seconds / 1e9,
+            "gsamples_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "makespan_s": makespan, "batches": info["batches"],
+            "saturation_gsamples_s": sat_rate, "saturation_vs_plain_fill": sat_rate / plain_rate,
+            "saturation_requests": len(sat),
+            "workload": "Poisson 20k req/s, log-uniform [2^10, 2^28], forms A/B/C, 2^16 clients x 16384 streams, "
+                        "32 GiB pool"}
+
+
 def e2e(torch, P, g, samples_step):
     """End to end through the public API: prng_fill_f64_host into pinned host memory (device
     slices generated and copied back inside the call), one full 2^30-sample step per call."""
@@ -357,9 +459,19 @@ def e2e(torch, P, g, samples_step):
         g.fill_f64_host(host, PER_STREAM, P.FORM_B_INTBITS)
     dt = (time.perf_counter() - t0) / reps
     del host
+    # the same call into pageable memory (staged slices and copies), for comparison
+    import numpy as np
+
+    pageable = np.empty(samples_step, dtype=np.float64)
+    g.fill_f64_host(pageable, PER_STREAM, P.FORM_B_INTBITS)
+    t0 = time.perf_counter()
+    g.fill_f64_host(pageable, PER_STREAM, P.FORM_B_INTBITS)
+    dt_pageable = time.perf_counter() - t0
+    del pageable
     return {"value": samples_step / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": samples_step * 8, "ms_per_step": dt * 1e3,
-            "api": "prng_fill_f64_host (pinned host buffer)"}
+            "api": "prng_fill_f64_host (pinned host buffer: direct device writes)",
+            "pageable_gsamples_s": samples_step / dt_pageable / 1e9}
 
 
 if __name__ == "__main__":

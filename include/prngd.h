@@ -105,9 +105,10 @@ int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_r
 
 /*
  * prng_fill_f64_host -- end-to-end fill into HOST memory: the same values as prng_fill_f64
- * (the streams advance identically), generated on the device in slices and copied to
- * `host_out` (n_streams * per_stream doubles, any host memory; pinned memory is fastest),
- * with generation of the next slice overlapping the copy of the previous one. The call
+ * (the streams advance identically) into `host_out` (n_streams * per_stream doubles). If
+ * host_out is pinned (page-locked and mapped for the device), one kernel writes it directly
+ * over the host link; otherwise the values are generated on the device in slices and copied
+ * back, the next slice being generated while the previous one is copied. The call
  * synchronises. host_rejects (nullable, host memory) receives per-stream reject counts.
  * Errors: PRNG_EINVAL, PRNG_ENOMEM (staging buffers), PRNG_ECUDA.
  */
@@ -199,7 +200,7 @@ typedef struct prng_request {
  * Resident requests of one batch must not share streams; batches on different CUDA streams
  * that use the same resident streams must be ordered by the caller.
  * Errors: PRNG_EINVAL (bad request, overlapping resident ranges, n out of range),
- * PRNG_EBUSY (all 4 batch slots still in flight: poll or wait, then retry), PRNG_ENOMEM,
+ * PRNG_EBUSY (all 16 batch slots still in flight: poll or wait, then retry), PRNG_ENOMEM,
  * PRNG_ECUDA.
  */
 int prng_submit(prng_t h, const prng_request* reqs, int n, uint64_t* ticket, void* cuda_stream);
@@ -217,6 +218,22 @@ int prng_wait(prng_t h, uint64_t ticket, double timeout_s);
  * for in-flight batches and re-captures the graphs on next use. */
 int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket);
 int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket);
+
+/*
+ * prng_batch_autotune -- pick the batch launch shape for requests of `form` with lengths in
+ * [length_lo, length_hi]. If table_path names a table with a line for this (GPU name, w,
+ * form, length range) and force == 0, that shape is applied without measuring. Otherwise
+ * every candidate (4 or 8 warps per block x 2..8 blocks per SM x 1, 2 or 8 items per ticket)
+ * is timed on a synthetic batch of 256 fresh requests with log-uniform lengths in the range
+ * (at most 2^30 outputs, in an 8 GiB scratch buffer the call allocates and frees), the fastest is
+ * applied and, if table_path is not NULL, appended to the table as
+ * "<key> <warps> <blocks> <items> <ms>". Outputs never depend on the shape.
+ * The chosen shape and its time (ms; -1 when read from the table) are returned through the
+ * nullable pointers. Errors: PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA.
+ */
+int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_hi, const char* table_path,
+                        int force, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket,
+                        double* best_ms);
 
 /*
  * Serving loop. A server keeps per-client generator state resident on the device and runs

@@ -125,9 +125,22 @@ static cudaError_t launch_form(const FillParams& p, const CUtensorMap* map, cuda
   return launch_w_form<0, FORM>(p, map, s);
 }
 
+// Host memory the device can address (pinned / registered); its device-side address in *dev.
+bool device_mapped_host(const void* p, void** dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return false;
+  if (dev) *dev = a.devicePointer;
+  return true;
+}
+
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                 uint64_t* rejects, cudaStream_t s, bool allow_tma) {
   if (n_streams == 0 || per_stream == 0) return PRNG_OK;
+  if (allow_tma && device_mapped_host(out, nullptr)) allow_tma = false;  // host memory: plain stores only
   FillParams p;
   p.state = state;
   p.n_streams = n_streams;

@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
+#include <string>
 #include <numeric>
 #include <vector>
 
@@ -17,14 +19,14 @@
 
 namespace prngd_host {
 
-static constexpr int kSlots = 4;
+static constexpr int kSlots = 16;
 
 struct BatchSlot {
   prngd::BatchDesc* h_desc = nullptr;  // pinned
-  uint64_t* h_prefix = nullptr;        // pinned
+  uint32_t* h_prefix = nullptr;        // pinned
   uint32_t* h_nreq = nullptr;          // pinned
   prngd::BatchDesc* d_desc = nullptr;
-  uint64_t* d_prefix = nullptr;
+  uint32_t* d_prefix = nullptr;
   uint32_t* d_nreq = nullptr;
   unsigned long long* d_ticket = nullptr;
   cudaEvent_t done = nullptr;
@@ -71,10 +73,10 @@ static int ensure_engine(prng_ctx* h) {
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   for (auto& s : b->slot) {
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_desc, sizeof(prngd::BatchDesc) * b->max_req);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_prefix, sizeof(uint64_t) * (b->max_req + 1));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_prefix, sizeof(uint32_t) * (b->max_req + 1));
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_nreq, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s.d_desc, sizeof(prngd::BatchDesc) * b->max_req);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_prefix, sizeof(uint64_t) * (b->max_req + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_prefix, sizeof(uint32_t) * (b->max_req + 1));
     if (e == cudaSuccess) e = cudaMalloc(&s.d_nreq, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s.d_ticket, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
@@ -99,7 +101,13 @@ BatchShape default_batch_shape(int num_sms) {
 template <int W>
 static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
   auto k = prngd::batch_kernel<W>;
-  const size_t smem = (size_t)sh.warps_per_block * 32 * prngd::kSlotPitch;
+  const size_t smem = (size_t)sh.warps_per_block * 32 * prngd::kSlotPitch + 4 * (PRNG_MAX_BATCH_REQUESTS + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   const unsigned grid = (unsigned)(num_sms * sh.blocks_per_sm);
   k<<<grid, sh.warps_per_block * 32, smem, s>>>(p);
   return cudaGetLastError();
@@ -122,7 +130,7 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, cudaStream_t s) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(prngd::BatchDesc) * b->max_req, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, sizeof(uint64_t) * (b->max_req + 1), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, sizeof(uint32_t) * (b->max_req + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, s);
@@ -181,6 +189,7 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
                   (unsigned long long)r.first_stream, (unsigned long long)r.n_streams,
                   (unsigned long long)h->n_streams);
     const uint64_t half = (r.length + 2 * r.n_streams - 1) / (2 * r.n_streams);
+    if (2 * half >= 0xFFFFFFFFull) return fail(PRNG_EINVAL, "resident request rows must hold fewer than 2^32 outputs");
     d.seed = 0;
     d.first_stream = r.first_stream;
     d.per_stream = 2 * half;
@@ -228,10 +237,11 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
   uint64_t acc = 0;
   for (int i = 0; i < n; ++i) {
     sl->h_desc[i] = d[order[i]];
-    sl->h_prefix[i] = acc;
+    sl->h_prefix[i] = (uint32_t)acc;
     acc += (d[order[i]].n_rows + 31) / 32;
+    if (acc >= 0xFFFFFFFFull) return fail(PRNG_EINVAL, "a batch holds fewer than 2^37 rows");
   }
-  for (int i = n; i <= b->max_req; ++i) sl->h_prefix[i] = acc;
+  for (int i = n; i <= b->max_req; ++i) sl->h_prefix[i] = (uint32_t)acc;
   *sl->h_nreq = (uint32_t)n;
   rc = ensure_graph(h, *sl);
   if (rc) return rc;
@@ -284,6 +294,144 @@ int get_batch_shape(prng_ctx* h, BatchShape* sh) {
   return PRNG_OK;
 }
 
+// ----------------------------------------------------------------- autotuner
+// Times each candidate launch shape on a synthetic batch of fresh requests whose lengths are
+// log-uniform in [lo, hi] (deterministic, at most 2^30 outputs in total) and keeps the fastest.
+// Results are cached in a text table, one line per key: "<key> <warps> <blocks> <items> <ms>".
+static std::string tune_key(prng_ctx* h, int form, uint64_t lo, uint64_t hi) {
+  cudaDeviceProp pr;
+  std::string name = "gpu";
+  if (cudaGetDeviceProperties(&pr, h->device) == cudaSuccess) name = pr.name;
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s|w=%d|form=%d|len=%llu-%llu", name.c_str(), h->w, form, (unsigned long long)lo,
+           (unsigned long long)hi);
+  return buf;
+}
+
+static bool table_lookup(const char* path, const std::string& key, BatchShape* sh) {
+  if (!path) return false;
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char k[256];
+  int a, b, c;
+  double ms;
+  bool found = false;
+  while (fscanf(f, "%255s %d %d %d %lf", k, &a, &b, &c, &ms) == 5)
+    if (key == k) {
+      *sh = BatchShape{a, b, c};
+      found = true;
+    }
+  fclose(f);
+  return found;
+}
+
+int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, int force, BatchShape* best_out,
+             double* best_ms) {
+  if (lo == 0 || hi < lo) return fail(PRNG_EINVAL, "length range");
+  const std::string key = tune_key(h, form, lo, hi);
+  BatchShape found;
+  if (!force && table_lookup(path, key, &found)) {
+    int rc = set_batch_shape(h, found);
+    if (rc) return rc;
+    *best_out = found;
+    if (best_ms) *best_ms = -1;
+    return PRNG_OK;
+  }
+  // synthetic batch
+  const int n = 256;
+  std::vector<uint64_t> len(n);
+  uint64_t total = 0, z = 0x2545F4914F6CDD1Dull;
+  for (int i = 0; i < n; ++i) {
+    z = z * 6364136223846793005ull + 1442695040888963407ull;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    len[i] = (uint64_t)std::exp(std::log((double)lo) + u * (std::log((double)hi) - std::log((double)lo)));
+    if (len[i] < lo) len[i] = lo;
+    total += (len[i] + 1) & ~1ull;
+  }
+  const uint64_t cap = 1ull << 30;  // about 2 ms per trial at full speed: long enough that tails do not decide
+  if (total > cap) {
+    const double f = (double)cap / total;
+    total = 0;
+    for (auto& L : len) {
+      L = std::max<uint64_t>(1, (uint64_t)(L * f));
+      total += (L + 1) & ~1ull;
+    }
+  }
+  uint64_t* scratch = nullptr;
+  cudaError_t e = cudaMalloc(&scratch, total * 8 + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PRNG_ENOMEM, "autotune scratch: %s", cudaGetErrorString(e));
+  }
+  std::vector<prng_request> reqs(n);
+  uint64_t off = 0, first = 0;
+  for (int i = 0; i < n; ++i) {
+    prng_request& r = reqs[i];
+    r = prng_request{};
+    r.kind = PRNG_REQ_FRESH;
+    r.form = form;
+    r.length = len[i];
+    r.seed = 1000 + i;
+    r.first_stream = first;
+    r.d_out = scratch + off;
+    first += (len[i] + 1023) / 1024;
+    off += (len[i] + 1) & ~1ull;
+  }
+  cudaStream_t st;
+  cudaEvent_t a, b;
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  const int W[] = {4, 8}, B[] = {2, 3, 4, 6, 8}, I[] = {1, 2, 8};
+  BatchShape best{8, 4, 1};
+  double best_t = 1e30;
+  int rc = PRNG_OK;
+  for (int wv : W)
+    for (int bv : B)
+      for (int iv : I) {
+        if (rc) break;
+        rc = set_batch_shape(h, BatchShape{wv, bv, iv});
+        uint64_t t = 0;
+        if (!rc) rc = submit(h, reqs.data(), n, &t, st);  // warm-up (captures the graph)
+        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PRNG_ECUDA, "autotune sync");
+        float times[3];
+        for (int k = 0; k < 3 && !rc; ++k) {
+          cudaEventRecord(a, st);
+          rc = submit(h, reqs.data(), n, &t, st);
+          cudaEventRecord(b, st);
+          if (!rc && cudaEventSynchronize(b) != cudaSuccess) rc = fail(PRNG_ECUDA, "autotune sync");
+          if (!rc) cudaEventElapsedTime(&times[k], a, b);
+        }
+        if (rc) break;
+        std::sort(times, times + 3);
+        if (times[1] < best_t) {
+          best_t = times[1];
+          best = BatchShape{wv, bv, iv};
+        }
+      }
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaStreamDestroy(st);
+  cudaFree(scratch);
+  if (rc) return rc;
+  rc = set_batch_shape(h, best);
+  if (rc) return rc;
+  if (path) {
+    FILE* f = fopen(path, "a");
+    if (f) {
+      fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), best.warps_per_block, best.blocks_per_sm, best.items_per_ticket,
+              best_t);
+      fclose(f);
+    }
+  }
+  *best_out = best;
+  if (best_ms) *best_ms = best_t;
+  return PRNG_OK;
+}
+
 }  // namespace prngd_host
 
 using namespace prngd_host;
@@ -319,6 +467,22 @@ int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int
   if (!h) return fail(PRNG_EINVAL, "null handle");
   BatchShape sh;
   int rc = get_batch_shape(h, &sh);
+  if (rc) return rc;
+  if (warps_per_block) *warps_per_block = sh.warps_per_block;
+  if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
+  if (items_per_ticket) *items_per_ticket = sh.items_per_ticket;
+  return PRNG_OK;
+}
+
+int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_hi, const char* table_path,
+                        int force, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket, double* best_ms) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR)
+    return fail(PRNG_EINVAL, "form %d", form);
+  int rc = check_handle_device(h);
+  if (rc) return rc;
+  BatchShape sh;
+  rc = autotune(h, form, length_lo, length_hi, table_path, force, &sh, best_ms);
   if (rc) return rc;
   if (warps_per_block) *warps_per_block = sh.warps_per_block;
   if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;

@@ -29,7 +29,7 @@ struct BatchDesc {       // 64 bytes, built on the host
 
 struct BatchParams {
   const BatchDesc* desc;          // n_req descriptors (longest rows first)
-  const uint64_t* item_prefix;    // n_req + 1 cumulative counts of 32-row items
+  const uint32_t* item_prefix;    // n_req + 1 cumulative counts of 32-row items (< 2^32)
   const uint32_t* n_req_dev;      // number of requests of this launch (device, so a captured graph can be replayed)
   unsigned long long* ticket;     // item counter, zeroed before each launch
   uint4* state;                   // the handle's resident streams
@@ -42,27 +42,49 @@ struct BatchParams {
 
 constexpr int kSlotPitch = 144;
 
-__device__ __forceinline__ uint64_t ld_shared_u64(uint32_t addr) {
-  uint64_t v;
-  asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
-  return v;
-}  // 128-byte row segment + 16 bytes of padding: conflict-free staging
+  // 128-byte row segment + 16 bytes of padding: conflict-free staging
 
-__device__ __forceinline__ void bulk_store_1d(uint64_t* dst, uint32_t src, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
-               : "memory");
+
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr) : "memory");
+  return v;
 }
 
-// One row (one stream) of `count` outputs into out_row, staged per 16 outputs in this lane's
-// shared slot and written with 1D bulk copies (rows start 16-byte aligned: even row length and
-// aligned base). An odd final output is written with a plain store.
+// One item: rows row0 .. row0 + 31 of a request, one per lane (rows past n_rows are idle).
+// Per chunk of 16 outputs each lane stages its values in its padded slot of the warp's tile,
+// then the warp writes the tile row by row: lane (r, q) stores 16 bytes at piece q of row
+// k*4 + r, so every store instruction covers four 128-byte row segments. Rows are 16-byte
+// aligned (even row length, aligned base); a row's odd last output is stored as 8 bytes.
 template <int W, int FORM>
-__device__ __forceinline__ void batch_row(XorShift128& st, uint32_t& rej, const FillParams& fp, uint64_t count,
-                                          uint64_t* out_row, uint32_t slot) {
-  for (uint64_t x0 = 0; x0 < count; x0 += kChunk) {
+__device__ __forceinline__ void batch_item(const BatchDesc& d, uint64_t row0, const BatchParams& bp,
+                                           const FillParams& fp, uint32_t tile, int lane) {
+  const uint64_t row = row0 + lane;
+  uint32_t count = 0;  // outputs of this lane's row (row length < 2^32, checked on the host)
+  if (row < d.n_rows) {
+    const uint64_t start = row * d.per_stream;
+    if (d.length > start) count = (uint32_t)(d.length - start < d.per_stream ? d.length - start : d.per_stream);
+  }
+  XorShift128 st{1u, 2u, 3u, 4u};
+  if (row < d.n_rows) {
+    if (d.resident) {
+      const uint4 s4 = bp.state[d.first_stream + row];
+      st = XorShift128{s4.x, s4.y, s4.z, s4.w};
+    } else {
+      st = seed_stream(d.seed, d.first_stream + row);
+    }
+  }
+  uint32_t rej = 0;
+  const uint32_t slot = tile + (uint32_t)lane * kSlotPitch;
+  // All rows of an item have the same length except in a request's last item.
+  const uint32_t c0 = __shfl_sync(0xffffffffu, count, 0);
+  const bool uniform = __all_sync(0xffffffffu, count == c0);
+  const uint32_t max_count = __reduce_max_sync(0xffffffffu, count);
+  const uint32_t q = (uint32_t)(lane & 7);
+  for (uint32_t x0 = 0; x0 < max_count; x0 += kChunk) {
     uint64_t v[kChunk];
-    const uint64_t left = count - x0;
-    if (left >= (uint64_t)kChunk) {
+    const uint32_t left = count > x0 ? count - x0 : 0u;
+    if (left >= (uint32_t)kChunk) {
       if constexpr ((W == 32 || W == 24) && FORM != kFormA) {
 #pragma unroll
         for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM>(st, rej, fp, v[j], v[j + 1]);
@@ -72,81 +94,78 @@ __device__ __forceinline__ void batch_row(XorShift128& st, uint32_t& rej, const 
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) v[j] = (j < (int)left) ? next_output<W, FORM>(st, rej, fp) : 0ull;
+      for (int j = 0; j < kChunk; ++j) v[j] = ((uint32_t)j < left) ? next_output<W, FORM>(st, rej, fp) : 0ull;
     }
-    const uint32_t n = left >= (uint64_t)kChunk ? (uint32_t)kChunk : (uint32_t)left;
-    const uint32_t even = n & ~1u;
-    bulk_wait_read<0>();  // this lane's previous copy has finished reading the slot
+    __syncwarp();  // the previous chunk's tile has been read
 #pragma unroll
     for (int c = 0; c < kChunk / 2; ++c) st_shared_v2(slot + 16u * c, v[2 * c], v[2 * c + 1]);
-    fence_async_shared();
-    if (even) {
-      bulk_store_1d(out_row + x0, slot, even * 8u);
-      bulk_commit();
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t r = (uint32_t)(k * 4) + ((uint32_t)lane >> 3);
+      const uint32_t cr = uniform ? c0 : __shfl_sync(0xffffffffu, count, (int)r);  // warp-uniform branch
+      const uint32_t rl = cr > x0 ? cr - x0 : 0u;  // outputs of row r in this chunk
+      if (2u * q < rl) {
+        uint64_t* dst = d.out + (row0 + r) * d.per_stream + x0 + 2u * q;
+        const uint4 val = ld_shared_v4(tile + r * kSlotPitch + 16u * q);
+        if (2u * q + 1u < rl) {
+          *(uint4*)dst = val;
+        } else {
+          *dst = ((uint64_t)val.y << 32) | val.x;
+        }
+      }
     }
-    if (n & 1u) out_row[x0 + n - 1] = ld_shared_u64(slot + 8u * (n - 1u));
   }
-}
-
-template <int W, int FORM>
-__device__ __forceinline__ void batch_item(const BatchDesc& d, uint64_t row, const BatchParams& bp,
-                                           const FillParams& fp, uint32_t slot) {
-  const bool active = row < d.n_rows;
-  uint64_t count = 0;
-  if (active) {
-    const uint64_t start = row * d.per_stream;
-    count = d.length > start ? (d.length - start < d.per_stream ? d.length - start : d.per_stream) : 0;
+  if (row < d.n_rows) {
+    if (d.resident) bp.state[d.first_stream + row] = make_uint4(st.x, st.y, st.z, st.w);
+    if (d.rejects) d.rejects[row] = rej;
   }
-  if (!active) return;
-  XorShift128 st;
-  if (d.resident) {
-    const uint4 s4 = bp.state[d.first_stream + row];
-    st = XorShift128{s4.x, s4.y, s4.z, s4.w};
-  } else {
-    st = seed_stream(d.seed, d.first_stream + row);
-  }
-  uint32_t rej = 0;
-  if (count) batch_row<W, FORM>(st, rej, fp, count, d.out + row * d.per_stream, slot);
-  if (d.resident) bp.state[d.first_stream + row] = make_uint4(st.x, st.y, st.z, st.w);
-  if (d.rejects) d.rejects[row] = rej;
 }
 
 // Persistent batch kernel: each warp repeatedly takes items_per_ticket items from the
-// counter; an item is located by binary search over the per-request item prefix.
+// counter. The per-request item prefix is copied into shared memory once per block; an item
+// is located by binary search there, or directly when it falls in the warp's last request.
 template <int W>
-__global__ void __launch_bounds__(256) batch_kernel(const BatchParams bp) {
+__global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
   extern __shared__ uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t slot = smem_addr(smem_raw) + (uint32_t)(warp * 32 + lane) * kSlotPitch;
+  const int warps = blockDim.x >> 5;
   const uint32_t n_req = *bp.n_req_dev;
-  const uint64_t total = bp.item_prefix[n_req];
+  uint32_t* prefix = (uint32_t*)(smem_raw + (size_t)warps * 32 * kSlotPitch);
+  for (uint32_t i = threadIdx.x; i <= n_req; i += blockDim.x) prefix[i] = bp.item_prefix[i];
+  __syncthreads();
+  const uint32_t tile = smem_addr(smem_raw) + (uint32_t)(warp * 32) * kSlotPitch;
+  const uint32_t total = prefix[n_req];
   FillParams fp;
   fp.dc = bp.dc;
   fp.scale = bp.scale;
   fp.w = bp.w;
   fp.one = bp.one;
+  uint32_t r = 0;
   for (;;) {
     unsigned long long first = 0;
     if (lane == 0) first = atomicAdd(bp.ticket, (unsigned long long)bp.items_per_ticket);
     first = __shfl_sync(0xffffffffu, first, 0);
     if (first >= total) break;
-    const uint64_t last = first + bp.items_per_ticket < total ? first + bp.items_per_ticket : total;
-    for (uint64_t item = first; item < last; ++item) {
-      uint32_t lo = 0, hi = n_req;  // largest r with prefix[r] <= item
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (bp.item_prefix[mid] <= item) lo = mid; else hi = mid;
+    const uint32_t last = (uint32_t)(first + bp.items_per_ticket < total ? first + bp.items_per_ticket : total);
+    for (uint32_t item = (uint32_t)first; item < last; ++item) {
+      if (item < prefix[r] || item >= prefix[r + 1]) {  // largest r with prefix[r] <= item
+        uint32_t lo = 0, hi = n_req;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (prefix[mid] <= item) lo = mid; else hi = mid;
+        }
+        r = lo;
       }
-      const BatchDesc d = bp.desc[lo];
-      const uint64_t row = (item - bp.item_prefix[lo]) * 32 + lane;
+      const BatchDesc d = bp.desc[r];
+      const uint64_t row0 = (uint64_t)(item - prefix[r]) * 32;
       switch (d.form) {
-        case kFormA: batch_item<W, kFormA>(d, row, bp, fp, slot); break;
-        case kFormC: batch_item<W, kFormC>(d, row, bp, fp, slot); break;
-        default: batch_item<W, kFormB>(d, row, bp, fp, slot); break;
+        case kFormA: batch_item<W, kFormA>(d, row0, bp, fp, tile, lane); break;
+        case kFormC: batch_item<W, kFormC>(d, row0, bp, fp, tile, lane); break;
+        default: batch_item<W, kFormB>(d, row0, bp, fp, tile, lane); break;
       }
     }
   }
-  bulk_wait_all();
 }
 
 }  // namespace prngd

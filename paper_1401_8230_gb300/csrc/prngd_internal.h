@@ -40,6 +40,7 @@ int check_handle_device(prng_ctx* h);
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                 uint64_t* rejects, cudaStream_t s, bool allow_tma);
 int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
+bool device_mapped_host(const void* p, void** dev);
 void release_aux(prng_ctx* h);
 void release_batch(prng_ctx* h);
 BatchShape default_batch_shape(int num_sms);

@@ -95,6 +95,7 @@ struct Req {
 };
 
 constexpr int kLanes = 2;                      // small / large requests
+constexpr int kMaxBatchesPerLane = 6;          // batches of one lane on the device at once
 constexpr uint64_t kLargeOutputs = 1ull << 20;  // requests above this go to the large lane
 
 }  // namespace
@@ -109,7 +110,12 @@ struct prng_server {
   std::deque<uint64_t> waiting[kLanes];              // admitted, not launched (arrival order)
   std::unordered_map<uint64_t, uint64_t> busy;       // client -> id on the device
   std::unordered_map<uint64_t, std::deque<uint64_t>> client_q;  // admitted, not launched, per client
-  std::vector<std::pair<uint64_t, std::vector<uint64_t>>> inflight;  // ticket -> ids
+  struct Inflight {
+    uint64_t ticket;
+    int lane;
+    std::vector<uint64_t> ids;
+  };
+  std::vector<Inflight> inflight;
   uint64_t launched_batches = 0, completed = 0, samples_done = 0;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -120,14 +126,14 @@ namespace {
 int harvest(prng_server* s) {
   for (size_t k = 0; k < s->inflight.size();) {
     int done = 0;
-    int rc = prng_poll(s->h, s->inflight[k].first, &done);
+    int rc = prng_poll(s->h, s->inflight[k].ticket, &done);
     if (rc) return rc;
     if (!done) {
       ++k;
       continue;
     }
     const double t = s->now();
-    for (uint64_t id : s->inflight[k].second) {
+    for (uint64_t id : s->inflight[k].ids) {
       Req& r = s->reqs[id];
       r.state = 2;
       r.t_done = t;
@@ -141,6 +147,9 @@ int harvest(prng_server* s) {
 }
 
 int launch_lane(prng_server* s, int lane) {
+  int lane_inflight = 0;
+  for (auto& f : s->inflight) lane_inflight += f.lane == lane;
+  if (lane_inflight >= kMaxBatchesPerLane) return PRNG_OK;
   std::vector<prng_request> batch;
   std::vector<uint64_t> ids;
   std::deque<uint64_t> keep;
@@ -185,7 +194,7 @@ int launch_lane(prng_server* s, int lane) {
     q.pop_front();
     if (q.empty()) s->client_q.erase(r.client);
   }
-  s->inflight.push_back({ticket, ids});
+  s->inflight.push_back({ticket, lane, ids});
   s->launched_batches++;
   return PRNG_OK;
 }

@@ -161,7 +161,7 @@ def test_batch_errors():
         # more batches than slots in flight: EBUSY, then fine after waiting
         big = torch.empty(2**24, dtype=torch.float64, device="cuda")
         tickets, busy = [], False
-        for k in range(12):
+        for k in range(40):
             try:
                 tickets.append(P.prng_submit(g.h, [P.fresh_request(big, 2**24, k, 0)]))
             except P.PrngError as err:
@@ -170,8 +170,23 @@ def test_batch_errors():
                 break
         for t in tickets:
             P.prng_wait(g.h, t, 60)
-        assert busy or len(tickets) == 12
+        assert busy or len(tickets) == 40
         P.prng_wait(g.h, P.prng_submit(g.h, [P.fresh_request(b, 10, 1, 0)]), 60)
+
+
+def test_autotune_table_roundtrip(tmp_path):
+    path = str(tmp_path / "tune.txt")
+    with P.Generator(1, 1, 32) as g:
+        best = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, 2**14, path)
+        assert best["ms"] > 0 and 1 <= best["warps_per_block"] <= 8
+        assert P.prng_batch_get_shape(g.h) == (best["warps_per_block"], best["blocks_per_sm"], best["items_per_ticket"])
+        again = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, 2**14, path)  # read back, no timing
+        assert again["ms"] == -1 and again["warps_per_block"] == best["warps_per_block"]
+        b = dev_buf(5001)
+        P.prng_wait(g.h, P.prng_submit(g.h, [P.fresh_request(b, 5001, 3, 7)]), 60)
+        want, _ = oracle_fresh(3, 7, 5001, 0, 32, P.FORM_B_INTBITS)
+        assert same(as_host(b, 5001, P.FORM_B_INTBITS), want)
+    assert open(path).read().count("\n") == 1
 
 
 def test_batched_workload_sampled():
