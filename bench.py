@@ -220,6 +220,10 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--batched-requests", type=int, default=4096, help="reduce for profiling runs")
+    ap.add_argument("--batched-hi", type=int, default=2**26, help="largest request length (profiling runs)")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default batch launch shape")
+    ap.add_argument("--stats-per-stream", type=int, default=2**16, help="fused-statistics outputs per stream")
     ap.add_argument("--n-streams", type=int, default=None, help="override the stream count (profiling runs)")
     ap.add_argument("--per-stream", type=int, default=None, help="override outputs per stream (profiling runs)")
     args = ap.parse_args()
@@ -297,7 +301,7 @@ def main():
             "roofline": roofline, "clocks": clk, "gpu_launches": args.steps}
 
     if rank == 0 and not args.no_extras:
-        line["forms"] = extras(torch, P, g, out, stream, peak)
+        line["forms"] = extras(torch, P, g, out, stream, peak, args.stats_per_stream)
     plain_rate = value / world
     if rank == 0 and not args.no_e2e:
         line["e2e"] = e2e(torch, P, g, samples_step)
@@ -305,7 +309,8 @@ def main():
     g.close()
     if rank == 0 and not args.no_batched:
         torch.cuda.empty_cache()
-        line["batched"] = batched(torch, P, stream, plain_rate)
+        line["batched"] = batched(torch, P, stream, plain_rate, args.batched_requests, args.batched_hi,
+                                  not args.no_autotune)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_served:
         line["served"] = served(torch, P, plain_rate, args.serve_seconds)
@@ -320,7 +325,7 @@ def main():
     return 0
 
 
-def extras(torch, P, g, out, stream, peak):
+def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
     """The other forms and modes on the same sizes (average device time of a few launches)."""
     res = {}
     n = N_STREAMS * PER_STREAM
@@ -348,11 +353,12 @@ def extras(torch, P, g, out, stream, peak):
     gs = P.Generator(SEED, N_STREAMS, 32)
     hist = torch.zeros(65536, dtype=torch.int64, device="cuda")
     sums = torch.zeros(8, dtype=torch.int64, device="cuda")
-    per = 1 << 16
+    per = stats_per_stream
     fn = lambda: gs.fused_stats(per, hist, sums, None, stream)  # noqa: E731
     fn()
     ms = sum(time_calls(torch, fn, 3, stream)) / 3
-    res["w32_fused_stats_2p36"] = {"gsamples_s": N_STREAMS * per / (ms * 1e-3) / 1e9, "ms": ms}
+    res["w32_fused_stats"] = {"gsamples_s": N_STREAMS * per / (ms * 1e-3) / 1e9, "ms": ms,
+                              "outputs": N_STREAMS * per, "note": "2^20 streams x per_stream, no store"}
     gs.close()
     return res
 
@@ -360,13 +366,13 @@ def extras(torch, P, g, out, stream, peak):
 TUNE_TABLE = os.path.join(ROOT, "paper_1401_8230_gb300", "lib", "autotune.txt")
 
 
-def batched(torch, P, stream, plain_rate):
+def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True):
     """4096 fresh requests, log-uniform lengths in [2^8, 2^26], own seeds and stream offsets,
     w = 32 form B, one persistent launch (graph replay) with the autotuned shape; against the
     same requests as 4096 single-request launches."""
     from paper_1401_8230_gb300 import workloads
 
-    spec = workloads.batched_requests(n=4096, lo=2**8, hi=2**26, seed=1)
+    spec = workloads.batched_requests(n=n_req, lo=2**8, hi=hi, seed=1)
     sizes = [(r["length"] + 1) // 2 * 2 for r in spec]
     total = sum(r["length"] for r in spec)
     g = P.Generator(SEED, 1, W)
@@ -375,8 +381,7 @@ def batched(torch, P, stream, plain_rate):
     for r, sz in zip(spec, sizes):
         reqs.append(P.fresh_request(pool[off:], r["length"], r["seed"], r["first_stream"], P.FORM_B_INTBITS))
         off += sz
-    tuned = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, 2**26, TUNE_TABLE)
-    import ctypes
+    tuned = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, hi, TUNE_TABLE) if tune else None
 
     arr = (P.Request * len(reqs))(*reqs)
 
