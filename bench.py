@@ -313,7 +313,13 @@ def main():
                                   not args.no_autotune)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_served:
-        line["served"] = served(torch, P, plain_rate, args.serve_seconds)
+        mix_rate = None
+        forms = line.get("forms", {})
+        if all(k in forms for k in ("w32_formA_fp64", "w32_formB_intbits", "w32_formC_f32pair")):
+            # plain-fill rate of the served form mix (a third of the outputs in each form)
+            mix_rate = 3.0 / sum(1.0 / forms[k]["gsamples_s"] for k in ("w32_formA_fp64", "w32_formB_intbits",
+                                                                         "w32_formC_f32pair"))
+        line["served"] = served(torch, P, plain_rate, args.serve_seconds, mix_rate)
         torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
@@ -416,7 +422,7 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True):
             "per_request_launches_ms": plain_ms, "shape": tuned, "graph": True}
 
 
-def served(torch, P, plain_rate, seconds):
+def served(torch, P, plain_rate, seconds, mix_rate=None):
     """Poisson arrivals at 20k requests/s for `seconds`, lengths log-uniform in [2^10, 2^28],
     form uniform over A/B/C, 2^16 clients with 16384 resident streams each (16 GiB of state),
     32 GiB output pool; requests replayed in real time by the library's serving loop. Then the
@@ -448,6 +454,8 @@ def served(torch, P, plain_rate, seconds):
             "gsamples_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
             "p99_ms": float(np.percentile(lat, 99) * 1e3), "makespan_s": makespan, "batches": info["batches"],
             "saturation_gsamples_s": sat_rate, "saturation_vs_plain_fill": sat_rate / plain_rate,
+            "plain_fill_of_form_mix_gsamples_s": mix_rate,
+            "saturation_vs_plain_fill_of_form_mix": (sat_rate / mix_rate) if mix_rate else None,
             "saturation_requests": len(sat),
             "workload": "Poisson 20k req/s, log-uniform [2^10, 2^28], forms A/B/C, 2^16 clients x 16384 streams, "
                         "32 GiB pool"}

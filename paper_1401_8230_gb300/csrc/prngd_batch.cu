@@ -23,11 +23,11 @@ static constexpr int kSlots = 16;
 
 struct BatchSlot {
   prngd::BatchDesc* h_desc = nullptr;  // pinned
-  uint32_t* h_prefix = nullptr;        // pinned
-  uint32_t* h_nreq = nullptr;          // pinned
+  CUtensorMap* h_maps = nullptr;       // pinned, one per descriptor
+  CUtensorMap* d_maps = nullptr;
+  uint32_t* h_meta = nullptr;          // pinned: n_req, then the item prefix
   prngd::BatchDesc* d_desc = nullptr;
-  uint32_t* d_prefix = nullptr;
-  uint32_t* d_nreq = nullptr;
+  uint32_t* d_meta = nullptr;
   unsigned long long* d_ticket = nullptr;
   cudaEvent_t done = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -52,11 +52,11 @@ void release_batch(prng_ctx* h) {
     if (s.exec) cudaGraphExecDestroy(s.exec);
     if (s.done) cudaEventDestroy(s.done);
     cudaFreeHost(s.h_desc);
-    cudaFreeHost(s.h_prefix);
-    cudaFreeHost(s.h_nreq);
+    cudaFreeHost(s.h_maps);
+    cudaFree(s.d_maps);
+    cudaFreeHost(s.h_meta);
     cudaFree(s.d_desc);
-    cudaFree(s.d_prefix);
-    cudaFree(s.d_nreq);
+    cudaFree(s.d_meta);
     cudaFree(s.d_ticket);
   }
   if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
@@ -73,11 +73,11 @@ static int ensure_engine(prng_ctx* h) {
   cudaError_t e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
   for (auto& s : b->slot) {
     if (e == cudaSuccess) e = cudaMallocHost(&s.h_desc, sizeof(prngd::BatchDesc) * b->max_req);
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_prefix, sizeof(uint32_t) * (b->max_req + 1));
-    if (e == cudaSuccess) e = cudaMallocHost(&s.h_nreq, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_meta, sizeof(uint32_t) * (b->max_req + 2));
+    if (e == cudaSuccess) e = cudaMallocHost(&s.h_maps, sizeof(CUtensorMap) * b->max_req);
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_maps, sizeof(CUtensorMap) * b->max_req);
     if (e == cudaSuccess) e = cudaMalloc(&s.d_desc, sizeof(prngd::BatchDesc) * b->max_req);
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_prefix, sizeof(uint32_t) * (b->max_req + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&s.d_nreq, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s.d_meta, sizeof(uint32_t) * (b->max_req + 2));
     if (e == cudaSuccess) e = cudaMalloc(&s.d_ticket, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming);
   }
@@ -101,7 +101,7 @@ BatchShape default_batch_shape(int num_sms) {
 template <int W>
 static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
   auto k = prngd::batch_kernel<W>;
-  const size_t smem = (size_t)sh.warps_per_block * 32 * prngd::kSlotPitch + 4 * (PRNG_MAX_BATCH_REQUESTS + 1);
+  const size_t smem = 1024 + (size_t)sh.warps_per_block * prngd::kTileBytes + 4 * (PRNG_MAX_BATCH_REQUESTS + 1);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
@@ -113,12 +113,14 @@ static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape&
   return cudaGetLastError();
 }
 
+// The captured part of a launch: reset the item counter, run the persistent kernel. The
+// descriptors and item prefix are copied before it (sized to the batch) by submit().
 static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, cudaStream_t s) {
   BatchEngine* b = h->batch;
   prngd::BatchParams p;
   p.desc = sl.d_desc;
-  p.item_prefix = sl.d_prefix;
-  p.n_req_dev = sl.d_nreq;
+  p.maps = sl.d_maps;
+  p.meta = sl.d_meta;
   p.ticket = sl.d_ticket;
   p.state = h->d_state;
   p.dc = h->dc;
@@ -126,20 +128,14 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, cudaStream_t s) {
   p.w = h->w;
   p.one = 1;
   p.items_per_ticket = (uint32_t)b->shape.items_per_ticket;
-  cudaError_t e = cudaMemcpyAsync(sl.d_nreq, sl.h_nreq, sizeof(uint32_t), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_desc, sl.h_desc, sizeof(prngd::BatchDesc) * b->max_req, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(sl.d_prefix, sl.h_prefix, sizeof(uint32_t) * (b->max_req + 1), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
+  cudaError_t e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, s);
   if (h->w == 24) return launch_batch_w<24>(p, b->shape, h->num_sms, s);
   return launch_batch_w<0>(p, b->shape, h->num_sms, s);
 }
 
-// Capture the slot's copy + reset + launch sequence once per launch shape; replays copy the
-// pinned staging as it is at replay time.
+// Capture the slot's reset + launch once per launch shape.
 static int ensure_graph(prng_ctx* h, BatchSlot& sl) {
   BatchEngine* b = h->batch;
   if (sl.exec && sl.cfg_version == b->cfg_version) return PRNG_OK;
@@ -183,6 +179,7 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
     d.per_stream = chunk;
     d.n_rows = (uint32_t)rows;
     d.resident = 0;
+    d.full_rows = (uint32_t)(r.length / chunk);
   } else if (r.kind == PRNG_REQ_RESIDENT) {
     if (r.n_streams == 0 || r.first_stream >= h->n_streams || r.n_streams > h->n_streams - r.first_stream)
       return fail(PRNG_EINVAL, "resident request streams [%llu, +%llu) outside the handle's %llu streams",
@@ -195,10 +192,10 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
     d.per_stream = 2 * half;
     d.n_rows = (uint32_t)r.n_streams;
     d.resident = 1;
+    d.full_rows = (uint32_t)std::min<uint64_t>(r.length / d.per_stream, r.n_streams);
   } else {
     return fail(PRNG_EINVAL, "request kind %d", r.kind);
   }
-  d.pad = 0;
   return PRNG_OK;
 }
 
@@ -235,17 +232,26 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return d[a].per_stream > d[c].per_stream; });
   uint64_t acc = 0;
+  sl->h_meta[0] = (uint32_t)n;
   for (int i = 0; i < n; ++i) {
     sl->h_desc[i] = d[order[i]];
-    sl->h_prefix[i] = (uint32_t)acc;
+    sl->h_meta[1 + i] = (uint32_t)acc;
     acc += (d[order[i]].n_rows + 31) / 32;
     if (acc >= 0xFFFFFFFFull) return fail(PRNG_EINVAL, "a batch holds fewer than 2^37 rows");
   }
-  for (int i = n; i <= b->max_req; ++i) sl->h_prefix[i] = (uint32_t)acc;
-  *sl->h_nreq = (uint32_t)n;
+  sl->h_meta[1 + n] = (uint32_t)acc;
+  for (int i = 0; i < n; ++i) {  // 2D maps of the full rows; a request without one uses plain stores
+    prngd::BatchDesc& q = sl->h_desc[i];
+    if (q.full_rows < 32 || !encode_out_map(&sl->h_maps[i], q.out, q.full_rows, q.per_stream)) q.full_rows = 0;
+  }
   rc = ensure_graph(h, *sl);
   if (rc) return rc;
-  cudaError_t e = cudaGraphLaunch(sl->exec, s);
+  cudaError_t e = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(prngd::BatchDesc) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl->d_maps, sl->h_maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(sl->d_meta, sl->h_meta, sizeof(uint32_t) * (n + 2), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(sl->exec, s);
   if (e == cudaSuccess) e = cudaEventRecord(sl->done, s);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "batch launch: %s", cudaGetErrorString(e));
   sl->ticket = b->next_ticket++;

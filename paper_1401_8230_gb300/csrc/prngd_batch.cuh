@@ -24,13 +24,15 @@ struct BatchDesc {       // 64 bytes, built on the host
   uint32_t n_rows;       // streams used
   int32_t form;          // kFormA / kFormB / kFormC
   uint32_t resident;     // 1: rows continue handle streams
-  uint32_t pad;
+  uint32_t full_rows;    // rows 0 .. full_rows-1 hold per_stream outputs and are covered by the
+                         // request's tensor map (0: no map, plain stores only)
 };
 
 struct BatchParams {
   const BatchDesc* desc;          // n_req descriptors (longest rows first)
-  const uint32_t* item_prefix;    // n_req + 1 cumulative counts of 32-row items (< 2^32)
-  const uint32_t* n_req_dev;      // number of requests of this launch (device, so a captured graph can be replayed)
+  const CUtensorMap* maps;        // one per descriptor: 2D map of its full rows (used when full_rows > 0)
+  const uint32_t* meta;           // meta[0] = n_req, meta[1 .. n_req + 1] = cumulative counts of
+                                  // 32-row items (< 2^32); device memory, so a captured graph replays
   unsigned long long* ticket;     // item counter, zeroed before each launch
   uint4* state;                   // the handle's resident streams
   DivConst dc;
@@ -45,6 +47,12 @@ constexpr int kSlotPitch = 144;
   // 128-byte row segment + 16 bytes of padding: conflict-free staging
 
 
+__device__ __forceinline__ void tma_store_2d_global_map(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map), "r"(src), "r"(x),
+               "r"(y)
+               : "memory");
+}
+
 __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
   uint4 v;
   asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr) : "memory");
@@ -52,13 +60,15 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
 }
 
 // One item: rows row0 .. row0 + 31 of a request, one per lane (rows past n_rows are idle).
-// Per chunk of 16 outputs each lane stages its values in its padded slot of the warp's tile,
-// then the warp writes the tile row by row: lane (r, q) stores 16 bytes at piece q of row
-// k*4 + r, so every store instruction covers four 128-byte row segments. Rows are 16-byte
-// aligned (even row length, aligned base); a row's odd last output is stored as 8 bytes.
+// Per chunk of 16 outputs each lane stages its values as row `lane` of the warp's 32 x 16
+// tile (128-byte swizzle: piece c of row r at r*128 + ((c ^ (r & 7)) * 16)). An item of 32 full
+// rows is written by one 2D tensor store of the tile through the request's map (columns past
+// per_stream are clipped). A request's last item is written by the warp row by row: lane
+// (r, q) stores piece q of row k*4 + r, so each store instruction covers four 128-byte row
+// segments; rows are 16-byte aligned and a row's odd last output is stored as 8 bytes.
 template <int W, int FORM>
-__device__ __forceinline__ void batch_item(const BatchDesc& d, uint64_t row0, const BatchParams& bp,
-                                           const FillParams& fp, uint32_t tile, int lane) {
+__device__ __forceinline__ void batch_item(const BatchDesc& d, const CUtensorMap* map, uint64_t row0,
+                                           const BatchParams& bp, const FillParams& fp, uint32_t tile, int lane) {
   const uint64_t row = row0 + lane;
   uint32_t count = 0;  // outputs of this lane's row (row length < 2^32, checked on the host)
   if (row < d.n_rows) {
@@ -75,12 +85,15 @@ __device__ __forceinline__ void batch_item(const BatchDesc& d, uint64_t row0, co
     }
   }
   uint32_t rej = 0;
-  const uint32_t slot = tile + (uint32_t)lane * kSlotPitch;
-  // All rows of an item have the same length except in a request's last item.
+  const bool by_tma = row0 + 32 <= d.full_rows;  // warp-uniform
+  if (by_tma && lane == 0)  // the map was rewritten by a host copy since an earlier batch may have used this slot
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
   const uint32_t c0 = __shfl_sync(0xffffffffu, count, 0);
   const bool uniform = __all_sync(0xffffffffu, count == c0);
   const uint32_t max_count = __reduce_max_sync(0xffffffffu, count);
   const uint32_t q = (uint32_t)(lane & 7);
+  const uint32_t my_row = tile + (uint32_t)lane * 128u;
+  const uint32_t sw = (uint32_t)(lane & 7);
   for (uint32_t x0 = 0; x0 < max_count; x0 += kChunk) {
     uint64_t v[kChunk];
     const uint32_t left = count > x0 ? count - x0 : 0u;
@@ -96,22 +109,32 @@ __device__ __forceinline__ void batch_item(const BatchDesc& d, uint64_t row0, co
 #pragma unroll
       for (int j = 0; j < kChunk; ++j) v[j] = ((uint32_t)j < left) ? next_output<W, FORM>(st, rej, fp) : 0ull;
     }
-    __syncwarp();  // the previous chunk's tile has been read
-#pragma unroll
-    for (int c = 0; c < kChunk / 2; ++c) st_shared_v2(slot + 16u * c, v[2 * c], v[2 * c + 1]);
+    if (lane == 0) bulk_wait_read<0>();  // the warp's last tensor store has read the tile
     __syncwarp();
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const uint32_t r = (uint32_t)(k * 4) + ((uint32_t)lane >> 3);
-      const uint32_t cr = uniform ? c0 : __shfl_sync(0xffffffffu, count, (int)r);  // warp-uniform branch
-      const uint32_t rl = cr > x0 ? cr - x0 : 0u;  // outputs of row r in this chunk
-      if (2u * q < rl) {
-        uint64_t* dst = d.out + (row0 + r) * d.per_stream + x0 + 2u * q;
-        const uint4 val = ld_shared_v4(tile + r * kSlotPitch + 16u * q);
-        if (2u * q + 1u < rl) {
-          *(uint4*)dst = val;
-        } else {
-          *dst = ((uint64_t)val.y << 32) | val.x;
+    for (int c = 0; c < kChunk / 2; ++c) st_shared_v2(my_row + (((uint32_t)c ^ sw) << 4), v[2 * c], v[2 * c + 1]);
+    if (by_tma) {
+      fence_async_shared();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d_global_map(map, tile, (int)x0, (int)row0);
+        bulk_commit();
+      }
+    } else {
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const uint32_t r = (uint32_t)(k * 4) + ((uint32_t)lane >> 3);
+        const uint32_t cr = uniform ? c0 : __shfl_sync(0xffffffffu, count, (int)r);  // warp-uniform branch
+        const uint32_t rl = cr > x0 ? cr - x0 : 0u;  // outputs of row r in this chunk
+        if (2u * q < rl) {
+          uint64_t* dst = d.out + (row0 + r) * d.per_stream + x0 + 2u * q;
+          const uint4 val = ld_shared_v4(tile + r * 128u + ((q ^ (r & 7u)) << 4));
+          if (2u * q + 1u < rl) {
+            *(uint4*)dst = val;
+          } else {
+            *dst = ((uint64_t)val.y << 32) | val.x;
+          }
         }
       }
     }
@@ -130,11 +153,12 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
   extern __shared__ uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
-  const uint32_t n_req = *bp.n_req_dev;
-  uint32_t* prefix = (uint32_t*)(smem_raw + (size_t)warps * 32 * kSlotPitch);
-  for (uint32_t i = threadIdx.x; i <= n_req; i += blockDim.x) prefix[i] = bp.item_prefix[i];
+  const uint32_t n_req = bp.meta[0];
+  const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;  // tiles 1024-byte aligned (swizzle)
+  const uint32_t tile = smem_addr(smem_raw) + pad + (uint32_t)warp * kTileBytes;
+  uint32_t* prefix = (uint32_t*)(smem_raw + pad + (size_t)warps * kTileBytes);
+  for (uint32_t i = threadIdx.x; i <= n_req; i += blockDim.x) prefix[i] = bp.meta[1 + i];
   __syncthreads();
-  const uint32_t tile = smem_addr(smem_raw) + (uint32_t)(warp * 32) * kSlotPitch;
   const uint32_t total = prefix[n_req];
   FillParams fp;
   fp.dc = bp.dc;
@@ -160,12 +184,13 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
       const BatchDesc d = bp.desc[r];
       const uint64_t row0 = (uint64_t)(item - prefix[r]) * 32;
       switch (d.form) {
-        case kFormA: batch_item<W, kFormA>(d, row0, bp, fp, tile, lane); break;
-        case kFormC: batch_item<W, kFormC>(d, row0, bp, fp, tile, lane); break;
-        default: batch_item<W, kFormB>(d, row0, bp, fp, tile, lane); break;
+        case kFormA: batch_item<W, kFormA>(d, bp.maps + r, row0, bp, fp, tile, lane); break;
+        case kFormC: batch_item<W, kFormC>(d, bp.maps + r, row0, bp, fp, tile, lane); break;
+        default: batch_item<W, kFormB>(d, bp.maps + r, row0, bp, fp, tile, lane); break;
       }
     }
   }
+  if (lane == 0) bulk_wait_all();
 }
 
 }  // namespace prngd

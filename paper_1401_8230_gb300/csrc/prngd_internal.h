@@ -1,6 +1,7 @@
 // prngd_internal.h -- the handle behind prng_t and helpers shared by the library's
 // translation units. Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +42,7 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
                 uint64_t* rejects, cudaStream_t s, bool allow_tma);
 int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
 bool device_mapped_host(const void* p, void** dev);
+bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream);
 void release_aux(prng_ctx* h);
 void release_batch(prng_ctx* h);
 BatchShape default_batch_shape(int num_sms);
