@@ -42,6 +42,22 @@ PROFILE = os.path.join(ROOT, "profiles", "fill_b32_bulk_2p30.txt")
 KERNEL_SOURCES = ["paper_1401_8230_gb300/csrc/prngd_fill.cuh", "paper_1401_8230_gb300/csrc/prngd_math.cuh"]
 
 
+def shard_seed(seed: int, rank: int, n_streams: int) -> int:
+    """Seed whose streams 0 .. n-1 are streams rank*n .. rank*n + n-1 of `seed`: stream s of a
+    seed uses splitmix64 positions 2s+1 and 2s+2 after it, so shifting the seed by 2*rank*n
+    gammas shifts every stream by rank*n."""
+    return (seed + 2 * rank * n_streams * GAMMA) % 2**64
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    """The largest value over all ranks (the job's time is its slowest rank's)."""
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_desc():
     if (N_STREAMS, PER_STREAM) == (1 << 20, 1024):
         name = ("bulk fill: 2^20 xorshift128 streams (seed 1) x 1024 outputs = 2^30 uniforms, "
@@ -248,8 +264,7 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    # rank r's streams are streams [r n, (r+1) n) of SEED: splitmix64 stream s of seed + 2 r n gamma
-    seed_r = (SEED + 2 * rank * N_STREAMS * GAMMA) % 2**64
+    seed_r = shard_seed(SEED, rank, N_STREAMS)  # rank r fills streams [r n, (r+1) n) of SEED
     stream = torch.cuda.current_stream()
     g = P.Generator(seed_r, N_STREAMS, W)
     out = torch.empty(N_STREAMS * PER_STREAM, dtype=torch.float64, device="cuda")
@@ -281,9 +296,7 @@ def main():
     total_ms = t_start.elapsed_time(t_end)
     launch_ms = [a.elapsed_time(b) for a, b in evs]
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(dist, total_ms, "cuda")
     samples_step = N_STREAMS * PER_STREAM
     value = world * samples_step * args.steps / (total_ms * 1e-3) / 1e9
     avg_launch_ms = sum(launch_ms) / len(launch_ms)
