@@ -182,16 +182,31 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
     v0 = fast24_bits(u1a, u2a, Ka);
     v1 = fast24_bits(u1b, u2b, Kb);
   }
+  if (__builtin_expect(ok == 0, 0)) {
+    // Almost always a small value (A < 2^22 at w = 32): the inline medium path. Rejects and
+    // values near a rounding boundary replay the pair exactly.
+    bool replay = true;
+    if constexpr (W == 32) {
+      replay = false;
+      const uint64_t Xa = fast32_X(st.x, st.y), Xb = fast32_X(st.z, st.w);
+      if (!fast32_ok(st.x, Xa)) {
+        if (medium32_ok(st.x, Xa, st.y)) v0 = medium32_bits(st.x, st.y, Xa); else replay = true;
+      }
+      if (!fast32_ok(st.z, Xb)) {
+        if (medium32_ok(st.z, Xb, st.w)) v1 = medium32_bits(st.z, st.w, Xb); else replay = true;
+      }
+    }
+    if (replay) {
+      const PairOut o = slow_pair<kFormB>(old.x, old.y, old.z, old.w, rej, W, p.dc);
+      v0 = o.v0;
+      v1 = o.v1;
+      rej = o.rej;
+      st = XorShift128{o.x, o.y, o.z, o.w};
+    }
+  }
   if (FORM == kFormC) {
     v0 = f32pair_from_bits(v0);
     v1 = f32pair_from_bits(v1);
-  }
-  if (__builtin_expect(ok == 0, 0)) {
-    const PairOut o = slow_pair<FORM>(old.x, old.y, old.z, old.w, rej, W, p.dc);
-    v0 = o.v0;
-    v1 = o.v1;
-    rej = o.rej;
-    st = XorShift128{o.x, o.y, o.z, o.w};
   }
 }
 

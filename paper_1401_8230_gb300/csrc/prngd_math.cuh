@@ -241,6 +241,38 @@ PRNGD_HD uint64_t fast32_bits(uint32_t u1, uint32_t u2, uint64_t X) {
   return ((uint64_t)mhi << 32) | mlo;
 }
 
+// Medium path for w = 32, small values: 1 <= A < 2^22, so I < 2^54 and the double needs bits
+// below I. One more series term gives floor(V 2^96) = I 2^32 + (X mod 2^32) + (Y >> 32) with
+// Y = 3B + 4A = X + u1 + u2 (35 bits), unless the low word of Y is within 16 of 2^32 (the
+// remaining tail is below 10 2^-32). The 96-bit value is shifted left so its top bit is bit 95;
+// the 54-bit integer part of V at its binade is then bits 95..42, rounded at bit 42 (V is
+// never a tie). Valid when medium32_ok holds (the X condition of the fast path included).
+PRNGD_HD bool medium32_ok(uint32_t u1, uint64_t X, uint32_t u2) {
+  const uint64_t Y = X + (uint64_t)u1 + (uint64_t)u2;
+  return ((uint32_t)(u1 - 2u) < 0x3FFFFFu) &  // 1 <= A < 2^22
+         ((uint32_t)X < 0xFFFFFFF8u) & ((uint32_t)Y < 0xFFFFFFF0u);
+}
+PRNGD_HD uint64_t medium32_bits(uint32_t u1, uint32_t u2, uint64_t X) {
+  const uint64_t Y = X + (uint64_t)u1 + (uint64_t)u2;
+  const uint64_t I = ((uint64_t)(u1 - 1u) << 32) + (uint64_t)u1 * 2u + (uint64_t)u2 - 1u + (X >> 32);
+  // T = I 2^32 + xlo + (Y >> 32), as words t2 t1 t0
+  const uint64_t low = (uint64_t)(uint32_t)X + (Y >> 32);
+  const uint32_t t0 = (uint32_t)low;
+  const uint64_t mid = (I & 0xFFFFFFFFull) + (low >> 32);
+  const uint32_t t1 = (uint32_t)mid;
+  const uint32_t t2 = (uint32_t)(I >> 32) + (uint32_t)(mid >> 32);  // in [1, 2^22]
+  const uint32_t p = 31u - (uint32_t)clz32(t2);
+  const uint32_t k = 31u - p;  // left shift that puts the top bit at 95, in [9, 31]
+  uint32_t n2 = k ? (t2 << k) | (t1 >> (32u - k)) : t2;
+  uint32_t n1 = k ? (t1 << k) | (t0 >> (32u - k)) : t1;
+  const uint32_t n1r = n1 + 1024u;  // + 2^42: round at bit 42
+  n2 += (n1r < n1) ? 1u : 0u;
+  n1 = n1r;
+  const uint32_t mlo = (n1 >> 11) | (n2 << 21);
+  const uint32_t mhi = (n2 >> 11) + ((p + 990u) << 20);  // V in [2^(p-32), 2^(p-31)): same exponent rule
+  return ((uint64_t)mhi << 32) | mlo;
+}
+
 // Fast path for w = 24. With eps = 2^-24,
 //   V 2^64 = A 2^40 + (B + 2A) 2^16 + (2B + 3A) 2^-8 + (3B + 4A) 2^-32 + tail,
 // tail < 9.01 2^-32. With K = (2B + 3A) 2^24 + (3B + 4A) (< 2^51) the integer part is
