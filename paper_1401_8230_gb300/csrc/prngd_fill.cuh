@@ -140,11 +140,17 @@ struct PairOut {
   uint32_t x, y, z, w, rej;
 };
 
-// Exact replay of two outputs from state (x, y, z, w): in-order rejects, exact conversion.
+// Exact replay of two outputs. (x, y, z, w) is the state after the pair's 4-draw block; it is
+// rewound 4 steps to the block's start, then the two outputs are redrawn with in-order
+// rejects and converted exactly.
 template <int FORM>
 __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t rej, int wbits,
                                           DivConst dc) {
   XorShift128 st{x, y, z, w};
+  xs_prev(st);
+  xs_prev(st);
+  xs_prev(st);
+  xs_prev(st);
   const uint32_t top = (wbits == 32) ? 0xFFFFFFFFu : ((1u << wbits) - 1u);
   uint64_t v[2];
 #pragma unroll
@@ -162,12 +168,11 @@ __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, ui
 }
 
 // Two outputs of a w = 32 or w = 24 stream (forms B and C) from one 4-draw block, with one
-// branch for the pair: when either output needs the exact path, the pair is replayed from
-// the block's starting state.
+// branch for the pair. A small value takes the inline medium path; a reject or a value near
+// a rounding boundary replays the pair exactly from the block's starting state.
 template <int W, int FORM>
 __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const FillParams& p, uint64_t& v0,
                                           uint64_t& v1) {
-  const XorShift128 old = st;
   xs_block4(st);
   uint32_t ok;
   if constexpr (W == 32) {
@@ -185,9 +190,8 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
   if (__builtin_expect(ok == 0, 0)) {
     // Almost always a small value (A < 2^22 at w = 32): the inline medium path. Rejects and
     // values near a rounding boundary replay the pair exactly.
-    bool replay = true;
+    bool replay = false;
     if constexpr (W == 32) {
-      replay = false;
       const uint64_t Xa = fast32_X(st.x, st.y), Xb = fast32_X(st.z, st.w);
       if (!fast32_ok(st.x, Xa)) {
         if (medium32_ok(st.x, Xa, st.y)) v0 = medium32_bits(st.x, st.y, Xa); else replay = true;
@@ -195,9 +199,18 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
       if (!fast32_ok(st.z, Xb)) {
         if (medium32_ok(st.z, Xb, st.w)) v1 = medium32_bits(st.z, st.w, Xb); else replay = true;
       }
+    } else {
+      const uint32_t u1a = st.x >> 8, u2a = st.y >> 8, u1b = st.z >> 8, u2b = st.w >> 8;
+      const uint64_t Ka = fast24_K(u1a, u2a), Kb = fast24_K(u1b, u2b);
+      if (!fast24_ok(u1a, Ka)) {
+        if (medium24_ok(u1a, Ka, u2a)) v0 = medium24_bits(u1a, u2a, Ka); else replay = true;
+      }
+      if (!fast24_ok(u1b, Kb)) {
+        if (medium24_ok(u1b, Kb, u2b)) v1 = medium24_bits(u1b, u2b, Kb); else replay = true;
+      }
     }
     if (replay) {
-      const PairOut o = slow_pair<kFormB>(old.x, old.y, old.z, old.w, rej, W, p.dc);
+      const PairOut o = slow_pair<kFormB>(st.x, st.y, st.z, st.w, rej, W, p.dc);
       v0 = o.v0;
       v1 = o.v1;
       rej = o.rej;

@@ -252,25 +252,29 @@ PRNGD_HD bool medium32_ok(uint32_t u1, uint64_t X, uint32_t u2) {
   return ((uint32_t)(u1 - 2u) < 0x3FFFFFu) &  // 1 <= A < 2^22
          ((uint32_t)X < 0xFFFFFFF8u) & ((uint32_t)Y < 0xFFFFFFF0u);
 }
+// Double bits of RN(V) from T = floor(V 2^96) = t2 2^64 + t1 2^32 + t0 with 1 <= t2 < 2^23:
+// shift T left so its top bit is bit 95; the 54-bit integer part of V at its binade is bits
+// 95..42, rounded at bit 42 (V is never a tie).
+PRNGD_HD uint64_t rn_bits_from_scaled96(uint32_t t2, uint32_t t1, uint32_t t0) {
+  const uint32_t p = 31u - (uint32_t)clz32(t2);
+  const uint32_t k = 31u - p;  // in [9, 31]
+  uint32_t n2 = (t2 << k) | (t1 >> (32u - k));
+  uint32_t n1 = (t1 << k) | (t0 >> (32u - k));
+  const uint32_t n1r = n1 + 1024u;  // + 2^42
+  n2 += (n1r < n1) ? 1u : 0u;
+  n1 = n1r;
+  const uint32_t mlo = (n1 >> 11) | (n2 << 21);
+  const uint32_t mhi = (n2 >> 11) + ((p + 990u) << 20);  // V in [2^(p-32), 2^(p-31))
+  return ((uint64_t)mhi << 32) | mlo;
+}
+
 PRNGD_HD uint64_t medium32_bits(uint32_t u1, uint32_t u2, uint64_t X) {
   const uint64_t Y = X + (uint64_t)u1 + (uint64_t)u2;
   const uint64_t I = ((uint64_t)(u1 - 1u) << 32) + (uint64_t)u1 * 2u + (uint64_t)u2 - 1u + (X >> 32);
   // T = I 2^32 + xlo + (Y >> 32), as words t2 t1 t0
   const uint64_t low = (uint64_t)(uint32_t)X + (Y >> 32);
-  const uint32_t t0 = (uint32_t)low;
   const uint64_t mid = (I & 0xFFFFFFFFull) + (low >> 32);
-  const uint32_t t1 = (uint32_t)mid;
-  const uint32_t t2 = (uint32_t)(I >> 32) + (uint32_t)(mid >> 32);  // in [1, 2^22]
-  const uint32_t p = 31u - (uint32_t)clz32(t2);
-  const uint32_t k = 31u - p;  // left shift that puts the top bit at 95, in [9, 31]
-  uint32_t n2 = k ? (t2 << k) | (t1 >> (32u - k)) : t2;
-  uint32_t n1 = k ? (t1 << k) | (t0 >> (32u - k)) : t1;
-  const uint32_t n1r = n1 + 1024u;  // + 2^42: round at bit 42
-  n2 += (n1r < n1) ? 1u : 0u;
-  n1 = n1r;
-  const uint32_t mlo = (n1 >> 11) | (n2 << 21);
-  const uint32_t mhi = (n2 >> 11) + ((p + 990u) << 20);  // V in [2^(p-32), 2^(p-31)): same exponent rule
-  return ((uint64_t)mhi << 32) | mlo;
+  return rn_bits_from_scaled96((uint32_t)(I >> 32) + (uint32_t)(mid >> 32), (uint32_t)mid, (uint32_t)low);
 }
 
 // Fast path for w = 24. With eps = 2^-24,
@@ -299,6 +303,23 @@ PRNGD_HD uint64_t fast24_bits(uint32_t u1, uint32_t u2, uint64_t K) {
   const uint32_t mlo = funnel_r(jlo, jhi, s + 1u);
   const uint32_t mhi = (jhi >> (s + 1u)) + ((p + 990u) << 20);
   return ((uint64_t)mhi << 32) | mlo;
+}
+
+// Medium path for w = 24, small values 1 <= A < 2^14 (I < 2^54): with c3 = 4B + 5A,
+//   floor(V 2^96) = I 2^32 + (K mod 2^32) + floor(c3 / 2^24)
+// unless the low 24 bits of c3 are within 16 of 2^24 (the tail is below 11.01 2^-24).
+PRNGD_HD bool medium24_ok(uint32_t u1, uint64_t K, uint32_t u2) {
+  const uint32_t c3 = 4u * u2 + 5u * u1 - 1u;  // 4B + 5A, < 2^28
+  return ((uint32_t)(u1 - 2u) < 0x3FFFu) &     // 1 <= A < 2^14
+         ((uint32_t)K < 0xFFFFFFF0u) & ((c3 & 0xFFFFFFu) < 0xFFFFF0u);
+}
+PRNGD_HD uint64_t medium24_bits(uint32_t u1, uint32_t u2, uint64_t K) {
+  const uint32_t A = u1 - 1u, B = u2 + 1u;
+  const uint32_t c3 = 4u * B + 5u * A;
+  const uint64_t I = ((uint64_t)A << 40) + ((uint64_t)(B + 2u * A) << 16) + (K >> 32);
+  const uint64_t low = (uint64_t)(uint32_t)K + (c3 >> 24);
+  const uint64_t mid = (I & 0xFFFFFFFFull) + (low >> 32);
+  return rn_bits_from_scaled96((uint32_t)(I >> 32) + (uint32_t)(mid >> 32), (uint32_t)mid, (uint32_t)low);
 }
 
 // Form C from the form-B bits d: hi = RN32(d) by rounding the 53-bit significand to 24 bits
