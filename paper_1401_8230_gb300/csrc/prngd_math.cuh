@@ -258,14 +258,11 @@ PRNGD_HD bool medium32_ok(uint32_t u1, uint64_t X, uint32_t u2) {
 PRNGD_HD uint64_t rn_bits_from_scaled96(uint32_t t2, uint32_t t1, uint32_t t0) {
   const uint32_t p = 31u - (uint32_t)clz32(t2);
   const uint32_t k = 31u - p;  // in [9, 31]
-  uint32_t n2 = (t2 << k) | (t1 >> (32u - k));
-  uint32_t n1 = (t1 << k) | (t0 >> (32u - k));
-  const uint32_t n1r = n1 + 1024u;  // + 2^42
-  n2 += (n1r < n1) ? 1u : 0u;
-  n1 = n1r;
-  const uint32_t mlo = (n1 >> 11) | (n2 << 21);
-  const uint32_t mhi = (n2 >> 11) + ((p + 990u) << 20);  // V in [2^(p-32), 2^(p-31))
-  return ((uint64_t)mhi << 32) | mlo;
+  const uint32_t n2 = (t2 << k) | (t1 >> (32u - k));
+  const uint32_t n1 = (t1 << k) | (t0 >> (32u - k));
+  const uint64_t q = ((((uint64_t)n2) << 32) | n1) >> 10;  // bits 95..42: in [2^53, 2^54)
+  const uint64_t mant = (q >> 1) + (q & 1);               // in [2^52, 2^53]; 2^53 carries into the exponent
+  return ((uint64_t)(p + 990u) << 52) + mant;             // V in [2^(p-32), 2^(p-31))
 }
 
 PRNGD_HD uint64_t medium32_bits(uint32_t u1, uint32_t u2, uint64_t X) {

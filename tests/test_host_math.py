@@ -1,0 +1,26 @@
+"""The CUDA library's per-output arithmetic (prngd_math.cuh, __host__ __device__) compiled for
+the host and compared with the oracle on cases random GPU streams almost never reach."""
+import os
+import shutil
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+import oracle
+
+
+def test_device_arithmetic_matches_oracle_on_edge_cases(tmp_path):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    orc = tmp_path / "orc.o"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-c", oracle._SRC, "-o", str(orc)], check=True)
+    exe = tmp_path / "math_check"
+    subprocess.run([gxx, "-std=c++17", "-O2", "-ffp-contract=off",
+                    "-I" + os.path.join(ROOT, "paper_1401_8230_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "host", "math_check.cpp"), str(orc), "-o", str(exe), "-lm"], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-2000:]
+    assert "bad 0" in out.stdout
