@@ -170,12 +170,16 @@ int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist, uint64_t* 
  *                     the same output.
  *  PRNG_REQ_RESIDENT: rows continue the handle's streams first_stream .. first_stream +
  *                     n_streams - 1 (device-resident state, advanced by the call). Row length
- *                     per = 2 * ceil(length / (2 * n_streams)); row j holds
- *                     min(per, max(0, length - j * per)) outputs.
+ *                     per = 16 * ceil(length / (16 * n_streams)); row j holds
+ *                     min(per, max(0, length - j * per)) outputs (trailing rows may be empty:
+ *                     their streams do not advance).
  *
  * The outputs never depend on the launch shape, on the batch a request is in, or on the
  * other requests of the batch. d_out: device pointer, 16-byte aligned, 8 * length bytes
  * (form C: interleaved float pairs). d_rejects (nullable, device): one reject count per row.
+ * Rate: rows are written in 128-byte segments, so d_out should be 128-byte aligned and a
+ * fresh request's chunk a multiple of 16; rows that start 16 bytes off a 32-byte sector
+ * boundary write partial sectors and run at about 0.6 of the full rate.
  */
 #define PRNG_REQ_FRESH 0
 #define PRNG_REQ_RESIDENT 1

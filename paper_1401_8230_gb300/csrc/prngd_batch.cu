@@ -30,9 +30,9 @@ struct BatchSlot {
   uint32_t* d_meta = nullptr;
   unsigned long long* d_ticket = nullptr;
   cudaEvent_t done = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};  // by kernel: mixed forms, A, B, C
+  int cfg_version[4] = {-1, -1, -1, -1};  // launch shape each graph was captured with
   uint64_t ticket = 0;      // ticket of the batch last launched from this slot
-  int cfg_version = -1;     // launch shape the graph was captured with
 };
 
 struct BatchEngine {
@@ -49,7 +49,8 @@ void release_batch(prng_ctx* h) {
   BatchEngine* b = h->batch;
   if (!b) return;
   for (auto& s : b->slot) {
-    if (s.exec) cudaGraphExecDestroy(s.exec);
+    for (auto& x : s.exec)
+      if (x) cudaGraphExecDestroy(x);
     if (s.done) cudaEventDestroy(s.done);
     cudaFreeHost(s.h_desc);
     cudaFreeHost(s.h_maps);
@@ -98,9 +99,9 @@ BatchShape default_batch_shape(int num_sms) {
   return s;
 }
 
-template <int W>
-static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
-  auto k = prngd::batch_kernel<W>;
+template <int W, int FORM_ALL>
+static cudaError_t launch_batch_wf(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
+  auto k = prngd::batch_kernel<W, FORM_ALL>;
   const size_t smem = 1024 + (size_t)sh.warps_per_block * prngd::kTileBytes + 4 * (PRNG_MAX_BATCH_REQUESTS + 1);
   static bool attr = false;
   if (!attr) {
@@ -113,9 +114,20 @@ static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape&
   return cudaGetLastError();
 }
 
+template <int W>
+static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, int form_all,
+                                  cudaStream_t s) {
+  switch (form_all) {
+    case prngd::kFormA: return launch_batch_wf<W, prngd::kFormA>(p, sh, num_sms, s);
+    case prngd::kFormB: return launch_batch_wf<W, prngd::kFormB>(p, sh, num_sms, s);
+    case prngd::kFormC: return launch_batch_wf<W, prngd::kFormC>(p, sh, num_sms, s);
+    default: return launch_batch_wf<W, -1>(p, sh, num_sms, s);
+  }
+}
+
 // The captured part of a launch: reset the item counter, run the persistent kernel. The
 // descriptors and item prefix are copied before it (sized to the batch) by submit().
-static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, cudaStream_t s) {
+static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaStream_t s) {
   BatchEngine* b = h->batch;
   prngd::BatchParams p;
   p.desc = sl.d_desc;
@@ -130,32 +142,33 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, cudaStream_t s) {
   p.items_per_ticket = (uint32_t)b->shape.items_per_ticket;
   cudaError_t e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, s);
-  if (h->w == 24) return launch_batch_w<24>(p, b->shape, h->num_sms, s);
-  return launch_batch_w<0>(p, b->shape, h->num_sms, s);
+  if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, form_all, s);
+  if (h->w == 24) return launch_batch_w<24>(p, b->shape, h->num_sms, form_all, s);
+  return launch_batch_w<0>(p, b->shape, h->num_sms, form_all, s);
 }
 
 // Capture the slot's reset + launch once per launch shape.
-static int ensure_graph(prng_ctx* h, BatchSlot& sl) {
+static int ensure_graph(prng_ctx* h, BatchSlot& sl, int form_all) {
   BatchEngine* b = h->batch;
-  if (sl.exec && sl.cfg_version == b->cfg_version) return PRNG_OK;
-  if (sl.exec) {
-    cudaGraphExecDestroy(sl.exec);
-    sl.exec = nullptr;
+  const int g_i = form_all + 1;  // -1 (mixed) -> 0, A -> 1, B -> 2, C -> 3
+  if (sl.exec[g_i] && sl.cfg_version[g_i] == b->cfg_version) return PRNG_OK;
+  if (sl.exec[g_i]) {
+    cudaGraphExecDestroy(sl.exec[g_i]);
+    sl.exec[g_i] = nullptr;
   }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
-  cudaError_t e2 = enqueue_batch(h, sl, b->capture_stream);
+  cudaError_t e2 = enqueue_batch(h, sl, form_all, b->capture_stream);
   e = cudaStreamEndCapture(b->capture_stream, &g);
   if (e2 != cudaSuccess || e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return fail(PRNG_ECUDA, "batch capture: %s", cudaGetErrorString(e2 != cudaSuccess ? e2 : e));
   }
-  e = cudaGraphInstantiate(&sl.exec, g, 0);
+  e = cudaGraphInstantiate(&sl.exec[g_i], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-  sl.cfg_version = b->cfg_version;
+  sl.cfg_version[g_i] = b->cfg_version;
   return PRNG_OK;
 }
 
@@ -185,11 +198,14 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
       return fail(PRNG_EINVAL, "resident request streams [%llu, +%llu) outside the handle's %llu streams",
                   (unsigned long long)r.first_stream, (unsigned long long)r.n_streams,
                   (unsigned long long)h->n_streams);
-    const uint64_t half = (r.length + 2 * r.n_streams - 1) / (2 * r.n_streams);
-    if (2 * half >= 0xFFFFFFFFull) return fail(PRNG_EINVAL, "resident request rows must hold fewer than 2^32 outputs");
+    // Rows of a multiple of 16 outputs: with a 128-byte aligned d_out every row starts on a
+    // 128-byte line, so each 16-output row segment is written as four whole 32-byte sectors.
+    const uint64_t sixteenths = (r.length + 16 * r.n_streams - 1) / (16 * r.n_streams);
+    if (16 * sixteenths >= 0xFFFFFFFFull)
+      return fail(PRNG_EINVAL, "resident request rows must hold fewer than 2^32 outputs");
     d.seed = 0;
     d.first_stream = r.first_stream;
-    d.per_stream = 2 * half;
+    d.per_stream = 16 * sixteenths;
     d.n_rows = (uint32_t)r.n_streams;
     d.resident = 1;
     d.full_rows = (uint32_t)std::min<uint64_t>(r.length / d.per_stream, r.n_streams);
@@ -244,14 +260,17 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
     prngd::BatchDesc& q = sl->h_desc[i];
     if (q.full_rows < 32 || !encode_out_map(&sl->h_maps[i], q.out, q.full_rows, q.per_stream)) q.full_rows = 0;
   }
-  rc = ensure_graph(h, *sl);
+  int form_all = d[0].form;  // one form for the whole batch selects a single-form kernel
+  for (int i = 1; i < n && form_all >= 0; ++i)
+    if (d[i].form != form_all) form_all = -1;
+  rc = ensure_graph(h, *sl, form_all);
   if (rc) return rc;
   cudaError_t e = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(prngd::BatchDesc) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl->d_maps, sl->h_maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl->d_meta, sl->h_meta, sizeof(uint32_t) * (n + 2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaGraphLaunch(sl->exec, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(sl->exec[form_all + 1], s);
   if (e == cudaSuccess) e = cudaEventRecord(sl->done, s);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "batch launch: %s", cudaGetErrorString(e));
   sl->ticket = b->next_ticket++;
@@ -302,7 +321,8 @@ int get_batch_shape(prng_ctx* h, BatchShape* sh) {
 
 // ----------------------------------------------------------------- autotuner
 // Times each candidate launch shape on a synthetic batch of fresh requests whose lengths are
-// log-uniform in [lo, hi] (deterministic, at most 2^30 outputs in total) and keeps the fastest.
+// log-uniform in [lo, hi] (deterministic, at most 2^30 outputs in total, 256-byte aligned
+// outputs) and keeps the fastest.
 // Results are cached in a text table, one line per key: "<key> <warps> <blocks> <items> <ms>".
 static std::string tune_key(prng_ctx* h, int form, uint64_t lo, uint64_t hi) {
   cudaDeviceProp pr;
@@ -333,6 +353,10 @@ static bool table_lookup(const char* path, const std::string& key, BatchShape* s
   return found;
 }
 
+// Outputs reserved for a request of L outputs in the tuning scratch: each request starts on a
+// 256-byte boundary, as separately allocated outputs would.
+static uint64_t slot_of(uint64_t L) { return (L + 31) & ~31ull; }
+
 int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, int force, BatchShape* best_out,
              double* best_ms) {
   if (lo == 0 || hi < lo) return fail(PRNG_EINVAL, "length range");
@@ -354,7 +378,7 @@ int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, 
     const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
     len[i] = (uint64_t)std::exp(std::log((double)lo) + u * (std::log((double)hi) - std::log((double)lo)));
     if (len[i] < lo) len[i] = lo;
-    total += (len[i] + 1) & ~1ull;
+    total += slot_of(len[i]);
   }
   const uint64_t cap = 1ull << 30;  // about 2 ms per trial at full speed: long enough that tails do not decide
   if (total > cap) {
@@ -362,7 +386,7 @@ int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, 
     total = 0;
     for (auto& L : len) {
       L = std::max<uint64_t>(1, (uint64_t)(L * f));
-      total += (L + 1) & ~1ull;
+      total += slot_of(L);
     }
   }
   uint64_t* scratch = nullptr;
@@ -383,7 +407,7 @@ int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, 
     r.first_stream = first;
     r.d_out = scratch + off;
     first += (len[i] + 1023) / 1024;
-    off += (len[i] + 1) & ~1ull;
+    off += slot_of(len[i]);
   }
   cudaStream_t st;
   cudaEvent_t a, b;

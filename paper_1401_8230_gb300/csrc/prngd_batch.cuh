@@ -59,97 +59,192 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
   return v;
 }
 
-// One item: rows row0 .. row0 + 31 of a request, one per lane (rows past n_rows are idle).
-// Per chunk of 16 outputs each lane stages its values as row `lane` of the warp's 32 x 16
-// tile (128-byte swizzle: piece c of row r at r*128 + ((c ^ (r & 7)) * 16)). An item of 32 full
-// rows is written by one 2D tensor store of the tile through the request's map (columns past
-// per_stream are clipped). A request's last item is written by the warp row by row: lane
-// (r, q) stores piece q of row k*4 + r, so each store instruction covers four 128-byte row
-// segments; rows are 16-byte aligned and a row's odd last output is stored as 8 bytes.
+// Generates the next kChunk outputs of the lane's row (all of them exist) and stages them as
+// row `lane` of the warp's tile (128-byte swizzle: piece c of row r at r*128 + ((c ^ (r & 7)) *
+// 16)). Four outputs per iteration of a loop that is not unrolled: with warps that drift apart
+// in a persistent launch, a fully unrolled chunk (eight pairs, each with its inline medium path)
+// no longer fits the instruction cache. Lane 0 waits for the warp's previous tensor store to
+// have read the tile before the first piece is written.
 template <int W, int FORM>
-__device__ __forceinline__ void batch_item(const BatchDesc& d, const CUtensorMap* map, uint64_t row0,
-                                           const BatchParams& bp, const FillParams& fp, uint32_t tile, int lane) {
-  const uint64_t row = row0 + lane;
-  uint32_t count = 0;  // outputs of this lane's row (row length < 2^32, checked on the host)
-  if (row < d.n_rows) {
-    const uint64_t start = row * d.per_stream;
-    if (d.length > start) count = (uint32_t)(d.length - start < d.per_stream ? d.length - start : d.per_stream);
-  }
-  XorShift128 st{1u, 2u, 3u, 4u};
-  if (row < d.n_rows) {
-    if (d.resident) {
-      const uint4 s4 = bp.state[d.first_stream + row];
-      st = XorShift128{s4.x, s4.y, s4.z, s4.w};
+__device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej, const FillParams& fp,
+                                                 uint32_t my_row, uint32_t sw, int lane) {
+#pragma unroll 1
+  for (uint32_t c = 0; c < (uint32_t)kChunk / 2; c += 2) {
+    uint64_t a0, a1, b0, b1;
+    if constexpr ((W == 32 || W == 24) && FORM != kFormA) {
+      next_pair<W, FORM>(st, rej, fp, a0, a1);
+      next_pair<W, FORM>(st, rej, fp, b0, b1);
     } else {
-      st = seed_stream(d.seed, d.first_stream + row);
+      a0 = next_output<W, FORM>(st, rej, fp);
+      a1 = next_output<W, FORM>(st, rej, fp);
+      b0 = next_output<W, FORM>(st, rej, fp);
+      b1 = next_output<W, FORM>(st, rej, fp);
+    }
+    if (c == 0) {  // warp-uniform
+      if (lane == 0) bulk_wait_read<0>();
+      __syncwarp();
+    }
+    st_shared_v2(my_row + ((c ^ sw) << 4), a0, a1);
+    st_shared_v2(my_row + (((c + 1u) ^ sw) << 4), b0, b1);
+  }
+}
+
+// The conversion constants of a batch launch, as the fill code takes them.
+__device__ __forceinline__ FillParams fill_params_of(const BatchParams& bp) {
+  FillParams fp;
+  fp.dc = bp.dc;
+  fp.scale = bp.scale;
+  fp.w = bp.w;
+  fp.one = bp.one;
+  return fp;
+}
+
+struct RowState {  // a row's stream and reject count, passed by value to out-of-line code
+  XorShift128 st;
+  uint32_t rej;
+};
+
+// Generates the lane's next min(left, kChunk) outputs (zeros after them) and stages them as
+// above; the whole chunk is written, after the same wait. Out of line: it runs once per row at
+// most, at the row's end. `bp` is the launch's grid constant.
+template <int W, int FORM>
+__device__ __noinline__ RowState stage_partial_chunk(RowState rs, const BatchParams& bp, uint32_t my_row,
+                                                     uint32_t sw, int lane, uint32_t left) {
+  const FillParams fp = fill_params_of(bp);
+  XorShift128 st = rs.st;
+  uint32_t rej = rs.rej;
+  uint64_t v[kChunk];
+#pragma unroll
+  for (int j = 0; j < kChunk; ++j) v[j] = ((uint32_t)j < left) ? next_output<W, FORM>(st, rej, fp) : 0ull;
+  if (lane == 0) bulk_wait_read<0>();
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < kChunk / 2; ++c) st_shared_v2(my_row + (((uint32_t)c ^ sw) << 4), v[2 * c], v[2 * c + 1]);
+  return RowState{st, rej};
+}
+
+// Stream state of row `row` of a request at its first output.
+__device__ __forceinline__ XorShift128 item_row_state(const BatchDesc* __restrict__ dp, const BatchParams& bp,
+                                                      uint64_t row) {
+  if (dp->resident) {
+    const uint4 s4 = bp.state[dp->first_stream + row];
+    return XorShift128{s4.x, s4.y, s4.z, s4.w};
+  }
+  return seed_stream(dp->seed, dp->first_stream + row);
+}
+
+// An item of 32 full rows (every row holds per_stream outputs): rows row0 .. row0 + 31 of a
+// request, one per lane. Per chunk of 16 outputs the warp stages its 32 x 16 tile and lane 0
+// writes it with one 2D tensor store through the request's map (columns past per_stream are
+// clipped).
+template <int W, int FORM>
+__device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
+                                                uint64_t row0, const BatchParams& bp, const FillParams& fp,
+                                                uint32_t tile, int lane) {
+  const uint64_t row = row0 + lane;
+  XorShift128 st = item_row_state(dp, bp, row);
+  uint32_t rej = 0;
+  const uint32_t my_row = tile + (uint32_t)lane * 128u;
+  const uint32_t sw = (uint32_t)(lane & 7);
+  if (lane == 0)  // the map was rewritten by a host copy since an earlier batch may have used this slot
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+  const uint32_t per = (uint32_t)dp->per_stream;
+#pragma unroll 1
+  for (uint32_t x0 = 0; x0 < per; x0 += kChunk) {
+    const uint32_t left = per - x0;
+    if (left >= (uint32_t)kChunk) {
+      stage_full_chunk<W, FORM>(st, rej, fp, my_row, sw, lane);
+    } else {
+      const RowState rs = stage_partial_chunk<W, FORM>(RowState{st, rej}, bp, my_row, sw, lane, left);
+      st = rs.st;
+      rej = rs.rej;
+    }
+    fence_async_shared();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_2d_global_map(map, tile, (int)x0, (int)row0);
+      bulk_commit();
     }
   }
+  if (dp->resident) bp.state[dp->first_stream + row] = make_uint4(st.x, st.y, st.z, st.w);
+  uint64_t* rejects = dp->rejects;
+  if (rejects) rejects[row] = rej;
+}
+
+// Any other item (a request's last rows: ragged, shorter, or past n_rows), kept out of line so
+// the hot loop above stays small. The warp stages the tile as above and stores it row by row:
+// lane (r, q) stores piece q of row k*4 + r, so each store instruction covers four 128-byte row
+// segments; rows are 16-byte aligned and a row's odd last output is stored as 8 bytes.
+template <int W, int FORM>
+__device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp, uint64_t row0, const BatchParams& bp,
+                                               uint32_t tile, int lane) {
+  const FillParams fp = fill_params_of(bp);
+  const uint64_t row = row0 + lane;
+  const uint32_t n_rows = dp->n_rows;
+  uint32_t count = 0;  // outputs of this lane's row (row length < 2^32, checked on the host)
+  XorShift128 st{1u, 2u, 3u, 4u};
+  if (row < n_rows) {
+    const uint64_t per = dp->per_stream, length = dp->length, start = row * per;
+    if (length > start) count = (uint32_t)(length - start < per ? length - start : per);
+    st = item_row_state(dp, bp, row);
+  }
   uint32_t rej = 0;
-  const bool by_tma = row0 + 32 <= d.full_rows;  // warp-uniform
-  if (by_tma && lane == 0)  // the map was rewritten by a host copy since an earlier batch may have used this slot
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+  const uint32_t my_row = tile + (uint32_t)lane * 128u;
+  const uint32_t sw = (uint32_t)(lane & 7);
   const uint32_t c0 = __shfl_sync(0xffffffffu, count, 0);
   const bool uniform = __all_sync(0xffffffffu, count == c0);
   const uint32_t max_count = __reduce_max_sync(0xffffffffu, count);
   const uint32_t q = (uint32_t)(lane & 7);
-  const uint32_t my_row = tile + (uint32_t)lane * 128u;
-  const uint32_t sw = (uint32_t)(lane & 7);
+#pragma unroll 1
   for (uint32_t x0 = 0; x0 < max_count; x0 += kChunk) {
-    uint64_t v[kChunk];
     const uint32_t left = count > x0 ? count - x0 : 0u;
-    if (left >= (uint32_t)kChunk) {
-      if constexpr ((W == 32 || W == 24) && FORM != kFormA) {
-#pragma unroll
-        for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM>(st, rej, fp, v[j], v[j + 1]);
-      } else {
-#pragma unroll
-        for (int j = 0; j < kChunk; ++j) v[j] = next_output<W, FORM>(st, rej, fp);
-      }
+    if (__all_sync(0xffffffffu, left >= (uint32_t)kChunk)) {
+      stage_full_chunk<W, FORM>(st, rej, fp, my_row, sw, lane);
     } else {
-#pragma unroll
-      for (int j = 0; j < kChunk; ++j) v[j] = ((uint32_t)j < left) ? next_output<W, FORM>(st, rej, fp) : 0ull;
+      const RowState rs = stage_partial_chunk<W, FORM>(RowState{st, rej}, bp, my_row, sw, lane, left);
+      st = rs.st;
+      rej = rs.rej;
     }
-    if (lane == 0) bulk_wait_read<0>();  // the warp's last tensor store has read the tile
     __syncwarp();
 #pragma unroll
-    for (int c = 0; c < kChunk / 2; ++c) st_shared_v2(my_row + (((uint32_t)c ^ sw) << 4), v[2 * c], v[2 * c + 1]);
-    if (by_tma) {
-      fence_async_shared();
-      __syncwarp();
-      if (lane == 0) {
-        tma_store_2d_global_map(map, tile, (int)x0, (int)row0);
-        bulk_commit();
-      }
-    } else {
-      __syncwarp();
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const uint32_t r = (uint32_t)(k * 4) + ((uint32_t)lane >> 3);
-        const uint32_t cr = uniform ? c0 : __shfl_sync(0xffffffffu, count, (int)r);  // warp-uniform branch
-        const uint32_t rl = cr > x0 ? cr - x0 : 0u;  // outputs of row r in this chunk
-        if (2u * q < rl) {
-          uint64_t* dst = d.out + (row0 + r) * d.per_stream + x0 + 2u * q;
-          const uint4 val = ld_shared_v4(tile + r * 128u + ((q ^ (r & 7u)) << 4));
-          if (2u * q + 1u < rl) {
-            *(uint4*)dst = val;
-          } else {
-            *dst = ((uint64_t)val.y << 32) | val.x;
-          }
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t r = (uint32_t)(k * 4) + ((uint32_t)lane >> 3);
+      const uint32_t cr = uniform ? c0 : __shfl_sync(0xffffffffu, count, (int)r);  // warp-uniform branch
+      const uint32_t rl = cr > x0 ? cr - x0 : 0u;  // outputs of row r in this chunk
+      if (2u * q < rl) {
+        uint64_t* dst = dp->out + (row0 + r) * dp->per_stream + x0 + 2u * q;
+        const uint4 val = ld_shared_v4(tile + r * 128u + ((q ^ (r & 7u)) << 4));
+        if (2u * q + 1u < rl) {
+          *(uint4*)dst = val;
+        } else {
+          *dst = ((uint64_t)val.y << 32) | val.x;
         }
       }
     }
   }
-  if (row < d.n_rows) {
-    if (d.resident) bp.state[d.first_stream + row] = make_uint4(st.x, st.y, st.z, st.w);
-    if (d.rejects) d.rejects[row] = rej;
+  if (row < n_rows) {
+    if (dp->resident) bp.state[dp->first_stream + row] = make_uint4(st.x, st.y, st.z, st.w);
+    uint64_t* rejects = dp->rejects;
+    if (rejects) rejects[row] = rej;
   }
+}
+
+template <int W, int FORM>
+__device__ __forceinline__ void batch_item(const BatchDesc* __restrict__ dp, const CUtensorMap* map, uint64_t row0,
+                                           const BatchParams& bp, const FillParams& fp, uint32_t tile, int lane) {
+  if (row0 + 32 <= dp->full_rows)  // warp-uniform
+    batch_item_full<W, FORM>(dp, map, row0, bp, fp, tile, lane);
+  else
+    batch_item_ragged<W, FORM>(dp, row0, bp, tile, lane);
 }
 
 // Persistent batch kernel: each warp repeatedly takes items_per_ticket items from the
 // counter. The per-request item prefix is copied into shared memory once per block; an item
 // is located by binary search there, or directly when it falls in the warp's last request.
-template <int W>
-__global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
+// FORM_ALL < 0: requests of any form (per-item switch); otherwise every request has FORM_ALL,
+// which keeps the code and its register footprint to one form.
+template <int W, int FORM_ALL>
+__global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ BatchParams bp) {
   extern __shared__ uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
@@ -160,11 +255,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
   for (uint32_t i = threadIdx.x; i <= n_req; i += blockDim.x) prefix[i] = bp.meta[1 + i];
   __syncthreads();
   const uint32_t total = prefix[n_req];
-  FillParams fp;
-  fp.dc = bp.dc;
-  fp.scale = bp.scale;
-  fp.w = bp.w;
-  fp.one = bp.one;
+  const FillParams fp = fill_params_of(bp);
   uint32_t r = 0;
   for (;;) {
     unsigned long long first = 0;
@@ -172,6 +263,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
     first = __shfl_sync(0xffffffffu, first, 0);
     if (first >= total) break;
     const uint32_t last = (uint32_t)(first + bp.items_per_ticket < total ? first + bp.items_per_ticket : total);
+#pragma unroll 1
     for (uint32_t item = (uint32_t)first; item < last; ++item) {
       if (item < prefix[r] || item >= prefix[r + 1]) {  // largest r with prefix[r] <= item
         uint32_t lo = 0, hi = n_req;
@@ -181,12 +273,16 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const BatchParams bp) {
         }
         r = lo;
       }
-      const BatchDesc d = bp.desc[r];
+      const BatchDesc* dp = bp.desc + r;
       const uint64_t row0 = (uint64_t)(item - prefix[r]) * 32;
-      switch (d.form) {
-        case kFormA: batch_item<W, kFormA>(d, bp.maps + r, row0, bp, fp, tile, lane); break;
-        case kFormC: batch_item<W, kFormC>(d, bp.maps + r, row0, bp, fp, tile, lane); break;
-        default: batch_item<W, kFormB>(d, bp.maps + r, row0, bp, fp, tile, lane); break;
+      if constexpr (FORM_ALL >= 0) {
+        batch_item<W, FORM_ALL>(dp, bp.maps + r, row0, bp, fp, tile, lane);
+      } else {
+        switch (dp->form) {
+          case kFormA: batch_item<W, kFormA>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          case kFormC: batch_item<W, kFormC>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          default: batch_item<W, kFormB>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+        }
       }
     }
   }

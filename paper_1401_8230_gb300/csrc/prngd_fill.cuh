@@ -42,7 +42,12 @@ __device__ __forceinline__ uint64_t slow_output(uint32_t u1, uint32_t u2, XorShi
   }
   const uint64_t n = numerator(u1, u2, p.w);
   if (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
-  const uint64_t bits = rn_bits_exact(n, p.dc);
+  uint64_t bits;
+  if constexpr (W == 32 || W == 24) {
+    bits = rn_bits_exact(n, divconst_for<W>());
+  } else {
+    bits = rn_bits_exact(n, p.dc);
+  }
   return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }
 
@@ -140,12 +145,13 @@ struct PairOut {
   uint32_t x, y, z, w, rej;
 };
 
-// Exact replay of two outputs. (x, y, z, w) is the state after the pair's 4-draw block; it is
-// rewound 4 steps to the block's start, then the two outputs are redrawn with in-order
-// rejects and converted exactly.
-template <int FORM>
-__device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t rej, int wbits,
-                                          DivConst dc) {
+// Exact replay of two outputs (w = 32 or 24). (x, y, z, w) is the state after the pair's 4-draw
+// block; it is rewound 4 steps to the block's start, then the two outputs are redrawn with
+// in-order rejects and converted exactly.
+template <int FORM, int W>
+__device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t rej) {
+  constexpr int wbits = W;
+  const DivConst dc = divconst_for<W>();
   XorShift128 st{x, y, z, w};
   xs_prev(st);
   xs_prev(st);
@@ -210,7 +216,7 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
       }
     }
     if (replay) {
-      const PairOut o = slow_pair<kFormB>(st.x, st.y, st.z, st.w, rej, W, p.dc);
+      const PairOut o = slow_pair<kFormB, W>(st.x, st.y, st.z, st.w, rej);
       v0 = o.v0;
       v1 = o.v1;
       rej = o.rej;

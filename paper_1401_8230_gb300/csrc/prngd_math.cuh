@@ -171,6 +171,18 @@ struct DivConst {
   int sh;           // 64 - 2w
 };
 
+// The constants for w = 32 and w = 24, fixed at compile time (D' = D 2^(64-2w); v as above; the
+// host test recomputes both from the definition).
+template <int W>
+PRNGD_HD DivConst divconst_for() {
+  static_assert(W == 32 || W == 24, "compile-time constants exist for w = 32 and w = 24");
+  if constexpr (W == 32) {
+    return DivConst{0xFFFFFFFE00000001ull, 0x200000003ull, 0};
+  } else {
+    return DivConst{0xFFFFFE0000010000ull, 0x20000030000ull, 16};
+  }
+}
+
 // Double bits of RN(V) for any w in [2, 32], exactly. Normalise n to m = n 2^c in
 // [2^63, 2^64); Y = m / D' lies in (1/2, 2) and V = Y 2^(sh - c). The 2-by-1 division of
 // m 2^53 (Y >= 1) or m 2^54 (Y < 1) by D' gives the 54-bit integer part q of Y 2^53 or

@@ -3,7 +3,7 @@
 //
 // Clients: client c owns the handle's streams [c S, (c+1) S). A request of length L from c
 // continues the first n = min(S, ceil(L / min_per_stream)) of them as one resident request
-// (rows of 2 ceil(L / 2n) outputs), so a request's result is fixed by the client's history
+// (rows of 16 ceil(L / 16n) outputs), so a request's result is fixed by the client's history
 // and the request itself, never by what else is in flight. A client has at most one request
 // on the device at a time; later requests of a busy client wait in order.
 //

@@ -45,6 +45,12 @@ static uint64_t want_rn(uint32_t u1, uint32_t u2, int w) { return bits_of(orc_va
 
 int main() {
   std::mt19937_64 rng(2024);
+  // 0. the compile-time division constants equal the ones derived at run time
+  {
+    const DivConst a = make_dc(32), b = divconst_for<32>(), c = make_dc(24), d = divconst_for<24>();
+    expect(a.d_norm == b.d_norm && a.v == b.v && a.sh == b.sh, 1, "divconst32", 32, 0);
+    expect(c.d_norm == d.d_norm && c.v == d.v && c.sh == d.sh, 1, "divconst24", 24, 0);
+  }
   // 1. exact division, every w, random and edge draws; form C from the exact bits
   for (int w = 2; w <= 32; ++w) {
     const DivConst dc = make_dc(w);

@@ -2,7 +2,7 @@
 
 A fresh request's output is streams first_stream .. of its seed, `chunk` outputs each,
 concatenated and cut at `length`; a resident request continues the handle's streams with
-rows of per = 2 ceil(L / 2n) outputs. Values, reject counts and the resident state advance
+rows of per = 16 ceil(L / 16n) outputs. Values, reject counts and the resident state advance
 must be identical to the oracle, whatever the batch, its other requests or the launch shape."""
 import numpy as np
 import pytest
@@ -38,7 +38,7 @@ def oracle_fresh(seed, first, length, chunk, w, form):
 def oracle_resident(states, length, w, form):
     """Expected output, rejects and new states of a resident request over `states`."""
     n = len(states)
-    per = 2 * ((length + 2 * n - 1) // (2 * n))
+    per = 16 * ((length + 16 * n - 1) // (16 * n))
     vals, rej, new = [], [], []
     for j, st in enumerate(states):
         cnt = max(0, min(per, length - j * per))

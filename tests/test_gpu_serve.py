@@ -24,7 +24,7 @@ class ClientModel:
 
     def request(self, L, form):
         n = min(self.S, -(-L // self.min_per))
-        per = 2 * -(-L // (2 * n))
+        per = 16 * -(-L // (16 * n))
         vals = []
         for j in range(n):
             cnt = max(0, min(per, L - j * per))
