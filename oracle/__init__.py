@@ -22,7 +22,9 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FORM_A, FORM_B, FORM_C, FORM_N = 0, 1, 2, 3
+FORM_A, FORM_B, FORM_C, FORM_N, FORM_L = 0, 1, 2, 3, 4
+# Mode bits: Eq. (5)/(6) map, 1 - z, Algorithm 1's single-redraw rejects (0: Eq. (4), pairs).
+MODE_EQ5, MODE_ONE_MINUS, MODE_SINGLE = 1, 2, 4
 
 _U64P = ctypes.POINTER(ctypes.c_uint64)
 _U32P = ctypes.POINTER(ctypes.c_uint32)
@@ -73,6 +75,15 @@ def lib() -> ctypes.CDLL:
             L.orc_fill_state.restype = ctypes.c_int
             L.orc_fill_state.argtypes = [_U32P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_fill_mode.restype = ctypes.c_int
+            L.orc_fill_mode.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_fill_state_mode.restype = ctypes.c_int
+            L.orc_fill_state_mode.argtypes = [_U32P, ctypes.c_uint64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_void_p, ctypes.c_void_p]
+            L.orc_values_mode.restype = ctypes.c_int
+            L.orc_values_mode.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
             L.orc_stats.restype = ctypes.c_int
             L.orc_stats.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                     ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
@@ -176,6 +187,17 @@ def stat_terms(n: np.ndarray, w: int) -> np.ndarray:
     return out
 
 
+def values_mode(u1: np.ndarray, u2: np.ndarray, w: int, form: int, mode: int) -> np.ndarray:
+    """Output of each accepted attempt (u1[i], u2[i]) in `form` under `mode`."""
+    u1 = np.ascontiguousarray(u1, dtype=np.uint32)
+    u2 = np.ascontiguousarray(u2, dtype=np.uint32)
+    out = _out_array(u1.size, form)
+    rc = lib().orc_values_mode(_ptr(u1), _ptr(u2), u1.size, w, form, mode, _ptr(out))
+    if rc != 0:
+        raise ValueError(f"orc_values_mode rc={rc}")
+    return out
+
+
 def _out_array(count: int, form: int) -> np.ndarray:
     if form == FORM_C:
         return np.zeros(2 * count, dtype=np.float32)
@@ -184,22 +206,22 @@ def _out_array(count: int, form: int) -> np.ndarray:
     return np.zeros(count, dtype=np.float64)
 
 
-def fill(seed: int, first_stream: int, n_streams: int, per_stream: int, w: int, form: int):
+def fill(seed: int, first_stream: int, n_streams: int, per_stream: int, w: int, form: int, mode: int = 0):
     """Stream-major fill; returns (out, rejects per stream)."""
     out = _out_array(n_streams * per_stream, form)
     rej = np.zeros(n_streams, dtype=np.uint64)
-    rc = lib().orc_fill(seed, first_stream, n_streams, per_stream, w, form, _ptr(out), _ptr(rej))
+    rc = lib().orc_fill_mode(seed, first_stream, n_streams, per_stream, w, form, mode, _ptr(out), _ptr(rej))
     if rc != 0:
         raise ValueError(f"orc_fill rc={rc}")
     return out, rej
 
 
-def fill_state(state, count: int, w: int, form: int):
+def fill_state(state, count: int, w: int, form: int, mode: int = 0):
     """Continue one stream from `state`; returns (out, rejects, new_state)."""
     st = np.array(state, dtype=np.uint32).copy()
     out = _out_array(count, form)
     rej = np.zeros(1, dtype=np.uint64)
-    rc = lib().orc_fill_state(st.ctypes.data_as(_U32P), count, w, form, _ptr(out), _ptr(rej))
+    rc = lib().orc_fill_state_mode(st.ctypes.data_as(_U32P), count, w, form, mode, _ptr(out), _ptr(rej))
     if rc != 0:
         raise ValueError(f"orc_fill_state rc={rc}")
     return out, int(rej[0]), st

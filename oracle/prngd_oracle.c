@@ -164,6 +164,45 @@ double orc_rn_ratio(uint64_t num, uint64_t den) {
     return ldexp((double)(uint64_t)q, -s);
 }
 
+/* Bit length of a nonzero 128-bit integer. */
+static int bitlen_u128(u128 v) {
+    uint64_t hi = (uint64_t)(v >> 64);
+    return hi ? 64 + bitlen_u64(hi) : bitlen_u64((uint64_t)v);
+}
+
+/* Round-to-nearest-even of (num/den) * 2^-e for 0 <= num < 2^128, 1 <= den < 2^64 and
+ * num/den < 2^64, from the same definition as orc_rn_ratio: the 53-bit integer part q of
+ * num*2^s/den, then the remainder against den/2. Returns 0.0 for num = 0. */
+static double rn_ratio128(u128 num, uint64_t den, int e) {
+    if (num == 0) return 0.0;
+    int s = 52 + bitlen_u64(den) - bitlen_u128(num);
+    u128 q, r, d;
+    for (;;) {
+        if (s >= 0) {
+            d = (u128)den;
+            q = (num << s) / d; /* num * 2^s < 2^54 den < 2^118: no overflow */
+            r = (num << s) % d;
+        } else {
+            if (-s > 63) return NAN; /* num/den >= 2^116: not used by this library */
+            d = (u128)den << (-s);
+            q = num / d;
+            r = num % d;
+        }
+        if (q >= ((u128)1 << 53)) {
+            --s;
+            continue;
+        }
+        if (q < ((u128)1 << 52)) {
+            ++s;
+            continue;
+        }
+        break;
+    }
+    u128 twice_r = r * 2;
+    if (twice_r > d || (twice_r == d && (q & 1))) q += 1;
+    return ldexp((double)(uint64_t)q, -s - e);
+}
+
 /* Form (b): the correctly rounded double nearest to z' = n / D_w. */
 double orc_value_rn(uint64_t n, int w) { return orc_rn_ratio(n, orc_denominator(w)); }
 
@@ -223,27 +262,144 @@ uint64_t orc_next_n(uint32_t st[4], int w, uint64_t* rejects) {
 #define ORC_FORM_B 1 /* double, correctly rounded */
 #define ORC_FORM_C 2 /* float pair (hi, lo) */
 #define ORC_FORM_N 3 /* the integer numerators n themselves (uint64) */
+#define ORC_FORM_L 4 /* double, Algorithm 1's literal FP64 evaluation */
 
-static int form_ok(int form) { return form >= 0 && form <= 3; }
+static int form_ok(int form) { return form >= 0 && form <= 4; }
+
+/* Modes, bit flags (0: the map of Eq. (4) and pair rejects).
+ * ORC_MODE_EQ5: the map of Eq. (5), which for one base generator on [0, 1 - k] is Eq. (6):
+ *   x1 = a0 + k and x2 = b0 go to 0, x1 = a - k and x2 = b go to 1 - k'. With x1 = a0 + u1 k,
+ *   x2 = b0 + u2 k and a - a0 = b - b0 = (2^w - 1) k, Eq. (5) reads
+ *       z' = (1 - k^2) ((u1 - 1) + u2 k) / ((2^w - 3) + (2^w - 1) k),
+ *   and scaling both parts by 2^w gives z' = (1 - k^2) m / (D_w - 2) with m = n - 1 =
+ *   (u1 - 1) 2^w + u2 in [0, D_w - 2]: the range is [0, 1 - k^2].
+ * ORC_MODE_ONE_MINUS: output 1 - z' instead of z' (Section 2: the usual way to exclude 0).
+ * ORC_MODE_SINGLE: Algorithm 1's reject loop, which redraws only r1 until it is accepted and
+ *   then draws r2 once; the default drops the whole pair ("take next pair", Section 2). */
+#define ORC_MODE_EQ5 1
+#define ORC_MODE_ONE_MINUS 2
+#define ORC_MODE_SINGLE 4
+
+static int mode_ok(int mode) { return mode >= 0 && mode <= 7; }
+
+/* Next accepted attempt (u1, u2) of a stream under the mode's reject rule. */
+static void next_attempt(uint32_t st[4], int w, int mode, uint64_t* rejects, uint32_t* u1,
+                         uint32_t* u2) {
+    if (mode & ORC_MODE_SINGLE) {
+        for (;;) {
+            *u1 = orc_draw(st, w);
+            if (orc_accept(*u1, w)) break;
+            ++*rejects;
+        }
+        *u2 = orc_draw(st, w);
+        return;
+    }
+    for (;;) {
+        *u1 = orc_draw(st, w);
+        *u2 = orc_draw(st, w);
+        if (orc_accept(*u1, w)) return;
+        ++*rejects;
+    }
+}
+
+/* The exact output value of an accepted attempt with numerator n (Eq. (4)) under the mode's
+ * map, rounded to nearest: Eq. (4) is n / D_w and its complement (D_w - n) / D_w; Eq. (5) is
+ * (2^2w - 1) m / ((D_w - 2) 2^2w) and its complement ((D_w - 2) 2^2w - (2^2w - 1) m) /
+ * ((D_w - 2) 2^2w), both exact integer ratios (u128). */
+static double value_mode_rn(uint64_t n, int w, int mode) {
+    uint64_t d = orc_denominator(w);
+    if (!(mode & ORC_MODE_EQ5)) return rn_ratio128((mode & ORC_MODE_ONE_MINUS) ? d - n : n, d, 0);
+    uint64_t m = n - 1, e = d - 2;
+    u128 p = ((u128)1 << (2 * w)) - 1;
+    u128 num = p * m;
+    if (mode & ORC_MODE_ONE_MINUS) num = ((u128)e << (2 * w)) - num;
+    return rn_ratio128(num, e, 2 * w);
+}
+
+/* Form (a) under a mode: the FP64 conversion sequence RN(RN(x) * C) of the map's integer
+ * numerator x and the compile-time constant C (Eq. (4): x = n, C = RN(1 / D_w); Eq. (5):
+ * x = m, C = RN((1 - k^2) / (D_w - 2))), then 1 - z as one more FP64 subtraction. */
+static double value_mode_form_a(uint64_t n, int w, int mode) {
+    volatile double z;
+    if (mode & ORC_MODE_EQ5) {
+        uint64_t e = orc_denominator(w) - 2;
+        volatile double c = rn_ratio128(((u128)1 << (2 * w)) - 1, e, 2 * w);
+        volatile double x = (double)(n - 1);
+        z = x * c;
+    } else {
+        z = orc_value_form_a(n, w);
+    }
+    if (mode & ORC_MODE_ONE_MINUS) z = 1.0 - z;
+    return z;
+}
+
+/* Form L: Algorithm 1 evaluated literally in FP64, one IEEE operation at a time (round to
+ * nearest even, no contraction), with the base PRNs R1 = u1 k and R2 = u2 k of one generator
+ * on [min, max] = [0, 1 - k] (exact doubles). Eq. (4) as Algorithm 1 writes it:
+ *     Z = (R1 + k R2 - (min + k max)) / ((max - min) (1 - k)),
+ * the constants min + k max and (max - min)(1 - k) folded once ("computed during
+ * compilation"). Eq. (5) through its one-generator form Eq. (6):
+ *     Z = (1 - k^2) (trunc[R1 / k] + R2 - 1) / (trunc[1 / k] - 2 - k).
+ * Then 1 - Z for ORC_MODE_ONE_MINUS. */
+static double value_mode_form_l(uint32_t u1, uint32_t u2, int w, int mode) {
+    volatile double k = ldexp(1.0, -w);
+    volatile double r1 = ldexp((double)u1, -w), r2 = ldexp((double)u2, -w);
+    volatile double mn = 0.0, mx = 1.0 - k;
+    volatile double z;
+    if (mode & ORC_MODE_EQ5) {
+        volatile double t = trunc(r1 / k);
+        volatile double s1 = t + r2;
+        volatile double s2 = s1 - 1.0;
+        volatile double kk = k * k;
+        volatile double c3 = 1.0 - kk;
+        volatile double num = c3 * s2;
+        volatile double t1 = trunc(1.0 / k);
+        volatile double d1 = t1 - 2.0;
+        volatile double den = d1 - k;
+        z = num / den;
+    } else {
+        volatile double kmx = k * mx;
+        volatile double c1 = mn + kmx;
+        volatile double span = mx - mn;
+        volatile double onek = 1.0 - k;
+        volatile double c2 = span * onek;
+        volatile double kr2 = k * r2;
+        volatile double a = r1 + kr2;
+        volatile double b = a - c1;
+        z = b / c2;
+    }
+    if (mode & ORC_MODE_ONE_MINUS) z = 1.0 - z;
+    return z;
+}
+
+/* One output of form `form` for the accepted attempt (u1, u2) under `mode`, written to
+ * element i of `out` (double, double, 2 floats, uint64, double). */
+static void put_output(uint32_t u1, uint32_t u2, int w, int form, int mode, void* out, uint64_t i) {
+    uint64_t n = orc_numerator(u1, u2, w);
+    switch (form) {
+        case ORC_FORM_A: ((double*)out)[i] = value_mode_form_a(n, w, mode); break;
+        case ORC_FORM_B: ((double*)out)[i] = value_mode_rn(n, w, mode); break;
+        case ORC_FORM_C: {
+            double d = value_mode_rn(n, w, mode);
+            volatile float h = (float)d;
+            volatile double rest = d - (double)h;
+            ((float*)out)[2 * i] = h;
+            ((float*)out)[2 * i + 1] = (float)rest;
+            break;
+        }
+        case ORC_FORM_L: ((double*)out)[i] = value_mode_form_l(u1, u2, w, mode); break;
+        default: ((uint64_t*)out)[i] = n; break;
+    }
+}
 
 /* Continue one stream from state `st` for `count` outputs. `out` receives count elements of
- * the form's type (double, double, 2 floats, uint64). */
-static void fill_from_state(uint32_t st[4], int w, int form, uint64_t count, void* out,
+ * the form's type. */
+static void fill_from_state(uint32_t st[4], int w, int form, int mode, uint64_t count, void* out,
                             uint64_t* rejects) {
     for (uint64_t i = 0; i < count; ++i) {
-        uint64_t n = orc_next_n(st, w, rejects);
-        switch (form) {
-            case ORC_FORM_A: ((double*)out)[i] = orc_value_form_a(n, w); break;
-            case ORC_FORM_B: ((double*)out)[i] = orc_value_rn(n, w); break;
-            case ORC_FORM_C: {
-                float h, l;
-                orc_value_form_c(n, w, &h, &l);
-                ((float*)out)[2 * i] = h;
-                ((float*)out)[2 * i + 1] = l;
-                break;
-            }
-            default: ((uint64_t*)out)[i] = n; break;
-        }
+        uint32_t u1, u2;
+        next_attempt(st, w, mode, rejects, &u1, &u2);
+        put_output(u1, u2, w, form, mode, out, i);
     }
 }
 
@@ -251,28 +407,39 @@ static size_t form_bytes(int form) { return (form == ORC_FORM_C) ? 8 : 8; }
 
 /* Stream-major fill: out[j * per_stream + i] is output i of stream first_stream + j, each
  * stream freshly seeded from (seed, stream id). rejects (nullable) gets one count per stream. */
-int orc_fill(uint64_t seed, uint64_t first_stream, uint64_t n_streams, uint64_t per_stream,
-             int w, int form, void* out, uint64_t* rejects) {
-    if (w < 2 || w > 32 || !form_ok(form) || (!out && n_streams && per_stream)) return ORC_EINVAL;
+int orc_fill_mode(uint64_t seed, uint64_t first_stream, uint64_t n_streams, uint64_t per_stream,
+                  int w, int form, int mode, void* out, uint64_t* rejects) {
+    if (w < 2 || w > 32 || !form_ok(form) || !mode_ok(mode) || (!out && n_streams && per_stream))
+        return ORC_EINVAL;
     for (uint64_t j = 0; j < n_streams; ++j) {
         uint32_t st[4];
         uint64_t rj = 0;
         orc_stream_seed(seed, first_stream + j, st);
-        fill_from_state(st, w, form, per_stream, (char*)out + j * per_stream * form_bytes(form),
-                        &rj);
+        fill_from_state(st, w, form, mode, per_stream,
+                        (char*)out + j * per_stream * form_bytes(form), &rj);
         if (rejects) rejects[j] = rj;
     }
     return ORC_OK;
 }
 
+int orc_fill(uint64_t seed, uint64_t first_stream, uint64_t n_streams, uint64_t per_stream,
+             int w, int form, void* out, uint64_t* rejects) {
+    return orc_fill_mode(seed, first_stream, n_streams, per_stream, w, form, 0, out, rejects);
+}
+
 /* One stream continued from a given state; the state is updated in place. */
-int orc_fill_state(uint32_t st[4], uint64_t count, int w, int form, void* out,
-                   uint64_t* rejects) {
-    if (w < 2 || w > 32 || !form_ok(form)) return ORC_EINVAL;
+int orc_fill_state_mode(uint32_t st[4], uint64_t count, int w, int form, int mode, void* out,
+                        uint64_t* rejects) {
+    if (w < 2 || w > 32 || !form_ok(form) || !mode_ok(mode)) return ORC_EINVAL;
     uint64_t r = 0;
-    fill_from_state(st, w, form, count, out, &r);
+    fill_from_state(st, w, form, mode, count, out, &r);
     if (rejects) *rejects = r;
     return ORC_OK;
+}
+
+int orc_fill_state(uint32_t st[4], uint64_t count, int w, int form, void* out,
+                   uint64_t* rejects) {
+    return orc_fill_state_mode(st, count, w, form, 0, out, rejects);
 }
 
 /* Fused statistics over streams first_stream .. first_stream + n_streams - 1, per_stream
@@ -333,4 +500,13 @@ void orc_values_form_c(const uint64_t* n, uint64_t count, int w, float* out) {
 }
 void orc_values_stat_terms(const uint64_t* n, uint64_t count, int w, uint64_t* out) {
     for (uint64_t i = 0; i < count; ++i) orc_stat_terms(n[i], w, &out[5 * i]);
+}
+
+/* Output of each accepted attempt (u1[i], u2[i]) in form `form` under `mode` (the reject bit
+ * is ignored: the attempts are given). */
+int orc_values_mode(const uint32_t* u1, const uint32_t* u2, uint64_t count, int w, int form,
+                    int mode, void* out) {
+    if (w < 2 || w > 32 || !form_ok(form) || !mode_ok(mode)) return ORC_EINVAL;
+    for (uint64_t i = 0; i < count; ++i) put_output(u1[i], u2[i], w, form, mode, out, i);
+    return ORC_OK;
 }
