@@ -357,6 +357,13 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
         ("w32_formA_fp64", lambda: g.fill_f64(out, PER_STREAM, P.FORM_A_FP64, None, stream)),
         ("w32_formB_intbits", lambda: g.fill_f64(out, PER_STREAM, P.FORM_B_INTBITS, None, stream)),
         ("w32_formC_f32pair", lambda: g.fill_f32pair(out, PER_STREAM, None, stream)),
+        # Section 2's other maps and Algorithm 1's literal FP64 evaluation
+        ("w32_eq5_formB", lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_EQ5, None, stream)),
+        ("w32_one_minus_formB", lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_ONE_MINUS, None, stream)),
+        ("w32_eq5_one_minus_formB",
+         lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_EQ5 | P.MODE_ONE_MINUS, None, stream)),
+        ("w32_formL_algorithm1_single_redraw",
+         lambda: g.fill_mode(out, PER_STREAM, P.FORM_L_ALGO1, P.MODE_SINGLE_REDRAW, None, stream)),
     ]:
         fn()
         ms = sum(time_calls(torch, fn, reps, stream)) / reps

@@ -54,6 +54,14 @@ extern "C" {
 #define PRNG_FORM_B_INTBITS 1 /* double RN(n/D), correctly rounded, built with integer ops  */
 #define PRNG_FORM_C_F32PAIR 2 /* two floats (hi, lo): hi = RN32(d), lo = RN32(d - hi), with */
                               /* d the form-B value; stored interleaved hi, lo               */
+#define PRNG_FORM_L_ALGO1 4   /* double: Algorithm 1's Z evaluated literally in FP64, one IEEE */
+                              /* operation at a time (prng_fill_mode only)                    */
+
+/* Modes of prng_fill_mode, bit flags (0 = the map of Eq. 4 with pair rejects). */
+#define PRNG_MODE_EQ5 1             /* the map of Eq. 5 (one generator: Eq. 6): z' = (1 - k^2) */
+                                    /* (n - 1)/(D - 2), range [0, 1 - k^2] with k = 2^-w        */
+#define PRNG_MODE_ONE_MINUS 2       /* output 1 - z' instead of z' (Section 2: excludes zero)  */
+#define PRNG_MODE_SINGLE_REDRAW 4   /* Algorithm 1's reject loop: redraw only r1, then draw r2  */
 
 typedef struct prng_ctx* prng_t;
 
@@ -102,6 +110,28 @@ int prng_fill_f64(prng_t h, double* d_out, uint64_t per_stream, int form, uint64
  */
 int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_rejects,
                       void* cuda_stream);
+
+/*
+ * prng_fill_mode -- as prng_fill_f64 / prng_fill_f32pair, for any form and mode.
+ * form: PRNG_FORM_A_FP64, PRNG_FORM_B_INTBITS, PRNG_FORM_C_F32PAIR (2 floats per output) or
+ * PRNG_FORM_L_ALGO1. mode: an OR of PRNG_MODE_* bits.
+ *  - PRNG_MODE_EQ5 (Section 2, Eq. 5 and Eq. 6): x1 = a0 + k, x2 = b0 map to 0 and
+ *    x1 = a - k, x2 = b to 1 - k^2; the output is (1 - k^2) m / (D - 2) with
+ *    m = (u1 - 1) 2^w + u2. Form B is its correctly rounded double, form A RN(RN(m) C5) with
+ *    C5 = RN((1 - k^2)/(D - 2)), form L Eq. 6 in FP64. At w = 32 the top value rounds to 1.0.
+ *  - PRNG_MODE_ONE_MINUS (Section 2): 1 - z'. Form B: the correctly rounded 1 - z' (under
+ *    Eq. 4 it equals z' of the complemented draws); forms A and L: one more FP64 subtraction.
+ *  - PRNG_MODE_SINGLE_REDRAW (Algorithm 1): a rejected r1 is redrawn alone and r2 is drawn
+ *    after the accepted r1; d_rejects then counts redrawn r1 values.
+ * Form L with PRNG_MODE_SINGLE_REDRAW is Algorithm 1 as printed. mode = 0 and forms A, B, C
+ * give exactly the outputs of prng_fill_f64 / prng_fill_f32pair. The streams advance as the
+ * reject rule consumes draws. d_out: device memory, 8-byte aligned; the fast (TMA) path needs
+ * 16-byte alignment and an even per_stream.
+ * Errors: PRNG_EINVAL (null handle or d_out, misaligned d_out, unknown form or mode bits),
+ * PRNG_ECUDA.
+ */
+int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mode, uint64_t* d_rejects,
+                   void* cuda_stream);
 
 /*
  * prng_fill_f64_host -- end-to-end fill into HOST memory: the same values as prng_fill_f64

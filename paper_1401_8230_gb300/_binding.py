@@ -8,7 +8,8 @@ import threading
 from . import build as _build
 
 PRNG_OK, PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA, PRNG_ETIMEOUT, PRNG_EBUSY, PRNG_ENOTFOUND = range(7)
-FORM_A_FP64, FORM_B_INTBITS, FORM_C_F32PAIR = 0, 1, 2
+FORM_A_FP64, FORM_B_INTBITS, FORM_C_F32PAIR, FORM_L_ALGO1 = 0, 1, 2, 4
+MODE_EQ5, MODE_ONE_MINUS, MODE_SINGLE_REDRAW = 1, 2, 4
 REQ_FRESH, REQ_RESIDENT = 0, 1
 MAX_BATCH_REQUESTS = 4096
 
@@ -49,6 +50,7 @@ _SIGNATURES = {
     "prng_get_info": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(_i32)]),
     "prng_fill_f64": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fill_f32pair": (_i32, [_P, _vp, _u64, _vp, _vp]),
+    "prng_fill_mode": (_i32, [_P, _vp, _u64, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "prng_fill_f64_host": (_i32, [_P, _vp, _u64, _i32, _vp]),
     "prng_fill_f64_host_noalloc": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
@@ -165,6 +167,10 @@ def prng_fill_f64(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, reje
 
 def prng_fill_f32pair(h: int, out, per_stream: int, rejects=None, stream=None) -> None:
     _check(lib().prng_fill_f32pair(h, _ptr(out), per_stream, _ptr(rejects), _stream(stream)))
+
+
+def prng_fill_mode(h: int, out, per_stream: int, form: int, mode: int, rejects=None, stream=None) -> None:
+    _check(lib().prng_fill_mode(h, _ptr(out), per_stream, form, mode, _ptr(rejects), _stream(stream)))
 
 
 def prng_fill_f64_host(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None) -> None:
@@ -317,6 +323,10 @@ class Generator:
 
     def fill_f32pair(self, out, per_stream: int, rejects=None, stream=None):
         prng_fill_f32pair(self.h, out, per_stream, rejects, stream)
+        return out
+
+    def fill_mode(self, out, per_stream: int, form: int, mode: int, rejects=None, stream=None):
+        prng_fill_mode(self.h, out, per_stream, form, mode, rejects, stream)
         return out
 
     def fill_f64_host(self, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None):

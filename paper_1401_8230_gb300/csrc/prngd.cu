@@ -50,6 +50,50 @@ DivConst make_divconst(int w) {
   return dc;
 }
 
+// Division constants of E = D - 2, the denominator of Eq. 5 (E is normalised by its own shift).
+DivConst make_divconst_eq5(int w) {
+  const uint64_t m = (w == 32) ? 0xFFFFFFFFull : ((1ull << w) - 1);
+  const uint64_t e = m * m - 2;
+  DivConst dc;
+  dc.sh = prngd::clz64(e);
+  dc.d_norm = e << dc.sh;
+  const unsigned __int128 all = ~(unsigned __int128)0;
+  dc.v = (uint64_t)(all / dc.d_norm - ((unsigned __int128)1 << 64));
+  return dc;
+}
+
+// The constants the map kernels take: C5 = RN((2^2w - 1) / ((D - 2) 2^2w)) for form A under
+// Eq. 5, and form L's folded constants, each one IEEE double operation as Algorithm 1 (Eq. 4)
+// or Eq. 6 writes them (volatile: no contraction, one rounding per operation).
+static void set_mode_constants(FillParams& p, int w, int mode) {
+  p.single = (mode & PRNG_MODE_SINGLE_REDRAW) ? 1u : 0u;
+  p.ec = make_divconst_eq5(w);
+  const int s2 = 2 * w;
+  const uint64_t num = (s2 == 64) ? ~0ull : ((1ull << s2) - 1);  // 2^2w - 1 (< 2^64)
+  const uint64_t c5 = prngd::rn_bits_ratio128(0, num, p.ec, s2);
+  memcpy(&p.scale5, &c5, 8);
+  volatile double k = std::ldexp(1.0, -w);
+  p.k = k;
+  if (mode & PRNG_MODE_EQ5) {
+    volatile double kk = k * k;
+    volatile double c3 = 1.0 - kk;
+    volatile double t1 = std::trunc(1.0 / k);
+    volatile double d1 = t1 - 2.0;
+    volatile double den = d1 - k;
+    p.l1 = c3;
+    p.l2 = den;
+  } else {
+    volatile double mn = 0.0, mx = 1.0 - k;
+    volatile double kmx = k * mx;
+    volatile double c1 = mn + kmx;
+    volatile double span = mx - mn;
+    volatile double onek = 1.0 - k;
+    volatile double c2 = span * onek;
+    p.l1 = c1;
+    p.l2 = c2;
+  }
+}
+
 double scale_constant(const DivConst& dc) {
   const uint64_t bits = prngd::rn_bits_exact(1, dc);  // RN(1/D)
   double d;
@@ -138,7 +182,7 @@ bool device_mapped_host(const void* p, void** dev) {
 }
 
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
-                uint64_t* rejects, cudaStream_t s, bool allow_tma) {
+                uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode) {
   if (n_streams == 0 || per_stream == 0) return PRNG_OK;
   if (allow_tma && device_mapped_host(out, nullptr)) allow_tma = false;  // host memory: plain stores only
   FillParams p;
@@ -151,9 +195,19 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
   p.scale = h->scale;
   p.w = h->w;
   p.one = 1;
+  set_mode_constants(p, h->w, mode);
   CUtensorMap map;
   const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
   cudaError_t e;
+  const int map_bits = mode & (PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS);
+  if (map_bits || form == PRNG_FORM_L_ALGO1) {
+    // Fast kernels: w = 32 / 24, forms B and C, TMA stores; everything else: the generic ones.
+    const bool fast = mp && (h->w == 32 || h->w == 24) &&
+                      (form == PRNG_FORM_B_INTBITS || form == PRNG_FORM_C_F32PAIR);
+    e = fast ? launch_fill_map_fast(p, form, map_bits, mp, s) : launch_fill_map(p, form, map_bits, mp, s);
+    if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));
+    return PRNG_OK;
+  }
   switch (form) {
     case PRNG_FORM_A_FP64: e = launch_form<prngd::kFormA>(p, mp, s); break;
     case PRNG_FORM_B_INTBITS: e = launch_form<prngd::kFormB>(p, mp, s); break;
@@ -268,6 +322,23 @@ int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_r
   if (rc) return rc;
   return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, PRNG_FORM_C_F32PAIR, d_rejects,
                      (cudaStream_t)cuda_stream, true);
+}
+
+int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mode, uint64_t* d_rejects,
+                   void* cuda_stream) {
+  if (!h) return fail(PRNG_EINVAL, "null handle");
+  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR &&
+      form != PRNG_FORM_L_ALGO1)
+    return fail(PRNG_EINVAL, "unknown form %d", form);
+  if (mode & ~(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
+    return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
+  if (per_stream == 0) return PRNG_OK;
+  if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
+  if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
+  int rc = check_handle_device(h);
+  if (rc) return rc;
+  return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, form, d_rejects, (cudaStream_t)cuda_stream,
+                     true, mode);
 }
 
 size_t prng_state_bytes(prng_t h) { return h ? (size_t)h->n_streams * 16 : 0; }

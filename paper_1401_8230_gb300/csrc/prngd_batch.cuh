@@ -71,7 +71,7 @@ __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej,
 #pragma unroll 1
   for (uint32_t c = 0; c < (uint32_t)kChunk / 2; c += 2) {
     uint64_t a0, a1, b0, b1;
-    if constexpr ((W == 32 || W == 24) && FORM != kFormA) {
+    if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
       next_pair<W, FORM>(st, rej, fp, a0, a1);
       next_pair<W, FORM>(st, rej, fp, b0, b1);
     } else {
@@ -96,6 +96,7 @@ __device__ __forceinline__ FillParams fill_params_of(const BatchParams& bp) {
   fp.scale = bp.scale;
   fp.w = bp.w;
   fp.one = bp.one;
+  fp.single = 0;
   return fp;
 }
 

@@ -13,7 +13,12 @@ namespace prngd {
 constexpr int kChunk = 16;         // outputs per stream per staged tile (128 bytes per row)
 constexpr int kTileBytes = 32 * kChunk * 8;  // one warp: 32 streams x 16 outputs x 8 bytes
 
-enum Form : int { kFormA = 0, kFormB = 1, kFormC = 2 };
+enum Form : int { kFormA = 0, kFormB = 1, kFormC = 2, kFormL = 4 };
+
+// Map bits (template parameter MAP of the per-output code): the map of Eq. 5 (one generator:
+// Eq. 6) instead of Eq. 4, and 1 - z instead of z. MAP = 0 is Eq. 4.
+constexpr int kMapEq5 = 1;
+constexpr int kMapOneMinus = 2;
 
 struct FillParams {
   uint4* state;         // n_streams xorshift states (x, y, z, w)
@@ -25,65 +30,148 @@ struct FillParams {
   double scale;         // C_w = RN(1/D) for form A
   int w;                // draw precision
   uint32_t one;         // always 1; a run-time multiplier keeps the adds below on the FMA pipe
+  uint32_t single;      // 1: Algorithm 1's reject loop (only r1 is redrawn); 0: the pair rule
+  DivConst ec;          // exact-division constants of D - 2 (Eq. 5)
+  double scale5;        // RN((1 - k^2) / (D - 2)), form A under Eq. 5
+  double k;             // 2^-w (form L)
+  double l1, l2;        // form L constants: Eq. 4: min + k max and (max - min)(1 - k);
+                        // Eq. 6: 1 - k^2 and trunc(1/k) - 2 - k
 };
 
 // ------------------------------------------------------------------------ per-output work
-// The slow path of one output: redraw rejected pairs in order, then convert exactly. Only
+// Rejects, in order (Section 2 and Algorithm 1): the pair rule drops (u1, u2) and takes the
+// next two draws; Algorithm 1's rule redraws only r1, so the pair's second draw is the next
+// r1 candidate and one more draw follows as r2.
+template <int W>
+__device__ __forceinline__ void take_accepted(uint32_t& u1, uint32_t& u2, XorShift128& st, uint32_t& rej, int w,
+                                              uint32_t top, uint32_t single) {
+  while (!accepted(u1, top)) {
+    ++rej;
+    if (single) {
+      u1 = u2;
+      u2 = draw<W>(st, w);
+    } else {
+      u1 = draw<W>(st, w);
+      u2 = draw<W>(st, w);
+    }
+  }
+}
+
+// Exactly rounded output bits (forms B and C) of an accepted pair at w = 32 or 24 under a map,
+// from compile-time constants only. Eq. 4's complement is Eq. 4 of the complemented draws.
+template <int W, int FORM, int MAP>
+__device__ __forceinline__ uint64_t exact_bc(uint32_t u1, uint32_t u2) {
+  constexpr uint32_t top = (W == 32) ? 0xFFFFFFFFu : ((1u << W) - 1u);
+  if constexpr ((MAP & kMapEq5) != 0) {
+    const uint64_t bits = eq5_bits_exact<W>(u1, u2, (MAP & kMapOneMinus) != 0);
+    if constexpr (FORM == kFormC) return bits ? f32pair_from_bits(bits) : 0ull;  // z' = 0 is a pair of zeros
+    return bits;
+  } else {
+    const uint32_t a1 = (MAP & kMapOneMinus) ? top - u1 : u1, a2 = (MAP & kMapOneMinus) ? top - u2 : u2;
+    const uint64_t bits = rn_bits_exact(numerator(a1, a2, W), divconst_for<W>());
+    return FORM == kFormC ? f32pair_from_bits(bits) : bits;
+  }
+}
+
+// Form L: Algorithm 1 evaluated literally in FP64 with the base PRNs R1 = u1 k and R2 = u2 k
+// (exact): Eq. 4 as (R1 + k R2 - (min + k max)) / ((max - min)(1 - k)); Eq. 5 through its
+// one-generator form Eq. 6, (1 - k^2)(trunc[R1/k] + R2 - 1) / (trunc[1/k] - 2 - k), where
+// trunc[R1/k] = u1. One IEEE operation at a time; the constants come folded from the host.
+template <int MAP>
+__device__ __forceinline__ uint64_t form_l_bits(uint32_t u1, uint32_t u2, const FillParams& p) {
+  const double r2 = __dmul_rn((double)u2, p.k);
+  double z;
+  if constexpr ((MAP & kMapEq5) != 0) {
+    const double s1 = __dadd_rn((double)u1, r2);
+    z = __ddiv_rn(__dmul_rn(p.l1, __dsub_rn(s1, 1.0)), p.l2);
+  } else {
+    const double a = __dadd_rn(__dmul_rn((double)u1, p.k), __dmul_rn(p.k, r2));
+    z = __ddiv_rn(__dsub_rn(a, p.l1), p.l2);
+  }
+  if constexpr ((MAP & kMapOneMinus) != 0) z = __dsub_rn(1.0, z);
+  return (uint64_t)__double_as_longlong(z);
+}
+
+// The output of an accepted pair, exactly as each form defines it, under a map.
+template <int W, int FORM, int MAP>
+__device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, const FillParams& p) {
+  const int w = W > 0 ? W : p.w;
+  if constexpr (FORM == kFormL) {
+    return form_l_bits<MAP>(u1, u2, p);
+  } else if constexpr (FORM == kFormA) {
+    double z;
+    if constexpr ((MAP & kMapEq5) != 0) {
+      z = __dmul_rn(__ull2double_rn(((uint64_t)(u1 - 1u) << w) + u2), p.scale5);  // RN(RN(m) C5)
+    } else {
+      z = __dmul_rn(__ull2double_rn(numerator(u1, u2, w)), p.scale);  // RN(RN(n) C_w)
+    }
+    if constexpr ((MAP & kMapOneMinus) != 0) z = __dsub_rn(1.0, z);
+    return (uint64_t)__double_as_longlong(z);
+  } else if constexpr (W == 32 || W == 24) {
+    return exact_bc<W, FORM, MAP>(u1, u2);
+  } else {
+    const uint32_t top = (w == 32) ? 0xFFFFFFFFu : ((1u << w) - 1u);
+    uint64_t bits;
+    if constexpr ((MAP & kMapEq5) != 0) {
+      bits = eq5_bits_exact_w(u1, u2, w, p.ec, (MAP & kMapOneMinus) != 0);
+      if constexpr (FORM == kFormC) return bits ? f32pair_from_bits(bits) : 0ull;
+      return bits;
+    } else {
+      const uint32_t a1 = (MAP & kMapOneMinus) ? top - u1 : u1, a2 = (MAP & kMapOneMinus) ? top - u2 : u2;
+      bits = rn_bits_exact(numerator(a1, a2, w), p.dc);
+    }
+    return FORM == kFormC ? f32pair_from_bits(bits) : bits;
+  }
+}
+
+// The slow path of one output: redraw rejected attempts in order, then convert exactly. Only
 // entered for a reject (probability 2^(1-w)), for small values (probability ~2^-10) and for
 // the rare values near a rounding boundary of the fast paths.
-template <int W, int FORM>
+template <int W, int FORM, int MAP = 0>
 __device__ __forceinline__ uint64_t slow_output(uint32_t u1, uint32_t u2, XorShift128& st, uint32_t& rej,
                                                 const FillParams& p) {
   const uint32_t top = (p.w == 32) ? 0xFFFFFFFFu : ((1u << p.w) - 1u);
-  while (!accepted(u1, top)) {
-    ++rej;
-    u1 = draw<W>(st, p.w);
-    u2 = draw<W>(st, p.w);
-  }
-  const uint64_t n = numerator(u1, u2, p.w);
-  if (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
-  uint64_t bits;
-  if constexpr (W == 32 || W == 24) {
-    bits = rn_bits_exact(n, divconst_for<W>());
-  } else {
-    bits = rn_bits_exact(n, p.dc);
-  }
-  return FORM == kFormC ? f32pair_from_bits(bits) : bits;
+  take_accepted<W>(u1, u2, st, rej, p.w, top, p.single);
+  return convert_exact<W, FORM, MAP>(u1, u2, p);
 }
 
 // One output of a stream, in order. Returns the 8 output bytes.
-template <int W, int FORM>
+template <int W, int FORM, int MAP = 0>
 __device__ __forceinline__ uint64_t next_output(XorShift128& st, uint32_t& rej, const FillParams& p) {
   const uint32_t u1 = draw<W>(st, p.w);
   const uint32_t u2 = draw<W>(st, p.w);
-  if (FORM == kFormA) {
+  if constexpr (FORM == kFormA || FORM == kFormL) {
     const uint32_t top = (W == 32) ? 0xFFFFFFFFu : (W > 0 ? ((1u << W) - 1u) : ((1u << p.w) - 1u));
-    if (__builtin_expect(accepted(u1, top), 1)) {
-      const int w = W > 0 ? W : p.w;
-      const uint64_t n = numerator(u1, u2, w);
-      return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
-    }
-    return slow_output<W, FORM>(u1, u2, st, rej, p);
-  }
-  uint64_t bits;
-  if (W == 32) {
-    const uint64_t X = fast32_X(u1, u2);
-    if (__builtin_expect(fast32_ok(u1, X), 1)) {
-      bits = fast32_bits(u1, u2, X);
-    } else {
-      return slow_output<W, FORM>(u1, u2, st, rej, p);
-    }
-  } else if (W == 24) {
-    const uint64_t K = fast24_K(u1, u2);
-    if (__builtin_expect(fast24_ok(u1, K), 1)) {
-      bits = fast24_bits(u1, u2, K);
-    } else {
-      return slow_output<W, FORM>(u1, u2, st, rej, p);
-    }
+    if (__builtin_expect(accepted(u1, top), 1)) return convert_exact<W, FORM, MAP>(u1, u2, p);
+    return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
+  } else if constexpr (W != 32 && W != 24) {
+    return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
   } else {
-    return slow_output<W, FORM>(u1, u2, st, rej, p);
+    constexpr bool kComp = (MAP & kMapOneMinus) != 0;
+    constexpr uint32_t top = (W == 32) ? 0xFFFFFFFFu : ((1u << W) - 1u);
+    const uint32_t a1 = kComp ? top - u1 : u1, a2 = kComp ? top - u2 : u2;  // 1 - z: complemented draws
+    uint64_t bits;
+    if constexpr ((MAP & kMapEq5) != 0) {
+      if constexpr (W == 32) {
+        const uint64_t Y = fast32_eq5_Y(a1, a2);
+        if (!__builtin_expect(fast32_eq5_ok(a1, Y), 1)) return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
+        bits = fast32_eq5_bits(a1, a2, Y, kComp ? 1u : 0u);
+      } else {
+        const uint64_t K = fast24_eq5_K(a1, a2);
+        if (!__builtin_expect(fast24_eq5_ok(a1, K), 1)) return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
+        bits = fast24_eq5_bits(a1, a2, K, kComp ? 0x10000u : 0u);
+      }
+    } else if constexpr (W == 32) {
+      const uint64_t X = fast32_X(a1, a2);
+      if (!__builtin_expect(fast32_ok(a1, X), 1)) return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
+      bits = fast32_bits(a1, a2, X);
+    } else {
+      const uint64_t K = fast24_K(a1, a2);
+      if (!__builtin_expect(fast24_ok(a1, K), 1)) return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
+      bits = fast24_bits(a1, a2, K);
+    }
+    return FORM == kFormC ? f32pair_from_bits(bits) : bits;
   }
-  return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }
 
 // ------------------------------------------------------------------------ pair fast path
@@ -100,29 +188,33 @@ __device__ __forceinline__ void xs_block4(XorShift128& s) {
   s.w = xs_word(s.w, s.z);
 }
 
-// The w = 32 form-B fast path of fast32_ok / fast32_bits written out as PTX, with the adds
-// that need no carry issued as multiply-adds by the run-time constant `one` so that they run
-// on the FMA pipe beside the ALU work of the draws. Returns 1 in `ok` when the fast path
-// applies (same condition as fast32_ok); the value is meaningless otherwise.
-__device__ __forceinline__ uint64_t fast32_bits_ptx(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
+// The w = 32 fast paths written out as PTX (Eq. 4: fast32_ok / fast32_bits; Eq. 5:
+// fast32_eq5_ok / fast32_eq5_bits), with the adds that need no carry issued as multiply-adds
+// by the run-time constant `one` so that they run on the FMA pipe beside the ALU work of the
+// draws. Both compute X = K1 u1 + 2 u2 + C0 and I = A 2^32 + 2A + u2 + (X >> 32) + PLUS:
+// Eq. 4 with (K1, C0, PLUS) = (3, -1, 1), X = 2B + 3A; Eq. 5 with (4, -4, 0 or 1), X = 4A + 2 u2.
+// Returns 1 in `ok` when 2^22 <= A <= 2^32 - 4 and the low word of X is below LIM; the value
+// is meaningless otherwise.
+template <int K1, int C0, int PLUS, unsigned LIM>
+__device__ __forceinline__ uint64_t fast32_bits_ptx_t(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
   uint32_t lo, hi;
   asm("{\n\t"
       ".reg .u64 Y, X, P, Ip;\n\t"
       ".reg .u32 xlo, f, a, A, g, ilo, ihi, q, s, rb, jlo, jhi, s1, mhi, e;\n\t"
       ".reg .pred p1, p2;\n\t"
-      "mad.wide.u32 Y, %4, 2, -1;\n\t"           // 2 u2 - 1
-      "mad.wide.u32 X, %3, 3, Y;\n\t"            // X = 2B + 3A = 3 u1 + 2 u2 - 1
+      "mad.wide.u32 Y, %4, 2, %6;\n\t"           // 2 u2 + C0
+      "mad.wide.u32 X, %3, %7, Y;\n\t"           // X = K1 u1 + 2 u2 + C0
       "mov.b64 {xlo, f}, X;\n\t"
       "mad.lo.u32 a, %3, %5, -4194305;\n\t"      // u1 - (2^22 + 1)
       "setp.lt.u32 p1, a, 0xFFBFFFFD;\n\t"       // 2^22 <= A <= 2^32 - 4
-      "setp.lt.and.u32 p2, xlo, 0xFFFFFFF8, p1;\n\t"
+      "setp.lt.and.u32 p2, xlo, %9, p1;\n\t"
       "selp.u32 %1, 1, 0, p2;\n\t"
       "mad.lo.u32 A, %3, %5, -1;\n\t"            // A = u1 - 1
       "mov.b64 P, {%4, A};\n\t"
       "mad.wide.u32 Ip, A, 2, P;\n\t"            // A 2^32 + u2 + 2A
-      "mad.lo.u32 g, f, %5, 1;\n\t"
+      "mad.lo.u32 g, f, %5, %8;\n\t"
       "mov.b64 {ilo, ihi}, Ip;\n\t"
-      "add.cc.u32 ilo, ilo, g;\n\t"              // I = A 2^32 + B + 2A + (X >> 32)
+      "add.cc.u32 ilo, ilo, g;\n\t"              // I = A 2^32 + u2 + 2A + (X >> 32) + PLUS
       "addc.u32 ihi, ihi, 0;\n\t"
       "bfind.u32 q, ihi;\n\t"                    // p, top bit of the high word
       "mad.lo.u32 s, q, %5, -21;\n\t"
@@ -136,8 +228,11 @@ __device__ __forceinline__ uint64_t fast32_bits_ptx(uint32_t u1, uint32_t u2, ui
       "mad.lo.u32 %0, mhi, %5, e;\n\t"
       "}"
       : "=r"(hi), "=r"(ok), "=r"(lo)
-      : "r"(u1), "r"(u2), "r"(one));
+      : "r"(u1), "r"(u2), "r"(one), "n"(C0), "n"(K1), "n"(PLUS), "n"(LIM));
   return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ uint64_t fast32_bits_ptx(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
+  return fast32_bits_ptx_t<3, -1, 1, 0xFFFFFFF8u>(u1, u2, one, ok);
 }
 
 struct PairOut {
@@ -147,11 +242,11 @@ struct PairOut {
 
 // Exact replay of two outputs (w = 32 or 24). (x, y, z, w) is the state after the pair's 4-draw
 // block; it is rewound 4 steps to the block's start, then the two outputs are redrawn with
-// in-order rejects and converted exactly.
-template <int FORM, int W>
-__device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t rej) {
+// in-order rejects (pair rule, or Algorithm 1's when `single`) and converted exactly.
+template <int FORM, int W, int MAP = 0>
+__device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t rej,
+                                          uint32_t single) {
   constexpr int wbits = W;
-  const DivConst dc = divconst_for<W>();
   XorShift128 st{x, y, z, w};
   xs_prev(st);
   xs_prev(st);
@@ -162,13 +257,8 @@ __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, ui
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
     uint32_t u1 = draw<0>(st, wbits), u2 = draw<0>(st, wbits);
-    while (!accepted(u1, top)) {
-      ++rej;
-      u1 = draw<0>(st, wbits);
-      u2 = draw<0>(st, wbits);
-    }
-    const uint64_t bits = rn_bits_exact(numerator(u1, u2, wbits), dc);
-    v[k] = FORM == kFormC ? f32pair_from_bits(bits) : bits;
+    take_accepted<0>(u1, u2, st, rej, wbits, top, single);
+    v[k] = exact_bc<W, FORM, MAP>(u1, u2);
   }
   return PairOut{v[0], v[1], st.x, st.y, st.z, st.w, rej};
 }
@@ -176,18 +266,63 @@ __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, ui
 // Two outputs of a w = 32 or w = 24 stream (forms B and C) from one 4-draw block, with one
 // branch for the pair. A small value takes the inline medium path; a reject or a value near
 // a rounding boundary replays the pair exactly from the block's starting state.
-template <int W, int FORM>
+template <int W, int FORM, int MAP = 0>
 __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const FillParams& p, uint64_t& v0,
                                           uint64_t& v1) {
   xs_block4(st);
+  // 1 - z: the arithmetic runs on the complemented draws (the state itself is not changed);
+  // complementing the 32-bit word complements its top w bits.
+  constexpr bool kComp = (MAP & kMapOneMinus) != 0;
+  const uint32_t dx = kComp ? ~st.x : st.x, dy = kComp ? ~st.y : st.y;
+  const uint32_t dz = kComp ? ~st.z : st.z, dw = kComp ? ~st.w : st.w;
   uint32_t ok;
+  if constexpr ((MAP & kMapEq5) != 0) {
+    // Eq. 5. At w = 32 small values take the inline medium path; rejects and boundary values
+    // (and at w = 24 small values) replay the pair exactly.
+    if constexpr (W == 32) {
+      uint32_t ok0, ok1;
+      v0 = fast32_bits_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(dx, dy, p.one, ok0);
+      v1 = fast32_bits_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(dz, dw, p.one, ok1);
+      ok = ok0 & ok1;
+    } else {
+      const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
+      const uint64_t Ka = fast24_eq5_K(u1a, u2a), Kb = fast24_eq5_K(u1b, u2b);
+      ok = fast24_eq5_ok(u1a, Ka) & fast24_eq5_ok(u1b, Kb);
+      v0 = fast24_eq5_bits(u1a, u2a, Ka, kComp ? 0x10000u : 0u);
+      v1 = fast24_eq5_bits(u1b, u2b, Kb, kComp ? 0x10000u : 0u);
+    }
+    if (__builtin_expect(ok == 0, 0)) {
+      bool replay = W != 32;
+      if constexpr (W == 32) {
+        const uint64_t Ya = fast32_eq5_Y(dx, dy), Yb = fast32_eq5_Y(dz, dw);
+        if (!fast32_eq5_ok(dx, Ya)) {
+          if (medium32_eq5_ok(dx, dy)) v0 = medium32_eq5_bits(dx, dy, Ya, kComp ? 1u : 0u); else replay = true;
+        }
+        if (!fast32_eq5_ok(dz, Yb)) {
+          if (medium32_eq5_ok(dz, dw)) v1 = medium32_eq5_bits(dz, dw, Yb, kComp ? 1u : 0u); else replay = true;
+        }
+      }
+      if (replay) {
+        const PairOut o = slow_pair<kFormB, W, MAP>(st.x, st.y, st.z, st.w, rej, p.single);
+        v0 = o.v0;
+        v1 = o.v1;
+        rej = o.rej;
+        st = XorShift128{o.x, o.y, o.z, o.w};
+      }
+    }
+    if (FORM == kFormC) {
+      v0 = v0 ? f32pair_from_bits(v0) : 0ull;  // z' = 0 is a pair of zeros
+      v1 = v1 ? f32pair_from_bits(v1) : 0ull;
+    }
+    return;
+  }
   if constexpr (W == 32) {
     uint32_t ok0, ok1;
-    v0 = fast32_bits_ptx(st.x, st.y, p.one, ok0);
-    v1 = fast32_bits_ptx(st.z, st.w, p.one, ok1);
+    v0 = fast32_bits_ptx(dx, dy, p.one, ok0);
+    v1 = fast32_bits_ptx(dz, dw, p.one, ok1);
     ok = ok0 & ok1;
   } else {
-    const uint32_t u1a = st.x >> 8, u2a = st.y >> 8, u1b = st.z >> 8, u2b = st.w >> 8;
+    const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
     const uint64_t Ka = fast24_K(u1a, u2a), Kb = fast24_K(u1b, u2b);
     ok = fast24_ok(u1a, Ka) & fast24_ok(u1b, Kb);
     v0 = fast24_bits(u1a, u2a, Ka);
@@ -198,15 +333,15 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
     // values near a rounding boundary replay the pair exactly.
     bool replay = false;
     if constexpr (W == 32) {
-      const uint64_t Xa = fast32_X(st.x, st.y), Xb = fast32_X(st.z, st.w);
-      if (!fast32_ok(st.x, Xa)) {
-        if (medium32_ok(st.x, Xa, st.y)) v0 = medium32_bits(st.x, st.y, Xa); else replay = true;
+      const uint64_t Xa = fast32_X(dx, dy), Xb = fast32_X(dz, dw);
+      if (!fast32_ok(dx, Xa)) {
+        if (medium32_ok(dx, Xa, dy)) v0 = medium32_bits(dx, dy, Xa); else replay = true;
       }
-      if (!fast32_ok(st.z, Xb)) {
-        if (medium32_ok(st.z, Xb, st.w)) v1 = medium32_bits(st.z, st.w, Xb); else replay = true;
+      if (!fast32_ok(dz, Xb)) {
+        if (medium32_ok(dz, Xb, dw)) v1 = medium32_bits(dz, dw, Xb); else replay = true;
       }
     } else {
-      const uint32_t u1a = st.x >> 8, u2a = st.y >> 8, u1b = st.z >> 8, u2b = st.w >> 8;
+      const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
       const uint64_t Ka = fast24_K(u1a, u2a), Kb = fast24_K(u1b, u2b);
       if (!fast24_ok(u1a, Ka)) {
         if (medium24_ok(u1a, Ka, u2a)) v0 = medium24_bits(u1a, u2a, Ka); else replay = true;
@@ -216,7 +351,7 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
       }
     }
     if (replay) {
-      const PairOut o = slow_pair<kFormB, W>(st.x, st.y, st.z, st.w, rej);
+      const PairOut o = slow_pair<kFormB, W, MAP>(st.x, st.y, st.z, st.w, rej, p.single);
       v0 = o.v0;
       v1 = o.v1;
       rej = o.rej;
@@ -258,7 +393,7 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint64_t a, uint64_t
 // * 16)), and lane 0 issues one 2D bulk tensor store of the 32 x 16 box. Rows past n_streams
 // and columns past per_stream fall outside the tensor and are not written. NBUF tiles per
 // warp let the next chunk's staging proceed while the previous store still reads shared memory.
-template <int W, int FORM, int NBUF>
+template <int W, int FORM, int NBUF, int MAP = 0>
 __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
                                                        const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smem_raw[];
@@ -281,16 +416,16 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
     uint64_t v[kChunk];
     const uint64_t left = p.per_stream - x0;
     if (left >= (uint64_t)kChunk) {
-      if constexpr ((W == 32 || W == 24) && FORM != kFormA) {
+      if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
 #pragma unroll
-        for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM>(st, rej, p, v[j], v[j + 1]);
+        for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM, MAP>(st, rej, p, v[j], v[j + 1]);
       } else {
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) v[j] = next_output<W, FORM>(st, rej, p);
+        for (int j = 0; j < kChunk; ++j) v[j] = next_output<W, FORM, MAP>(st, rej, p);
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < kChunk; ++j) v[j] = (j < (int)left) ? next_output<W, FORM>(st, rej, p) : 0ull;
+      for (int j = 0; j < kChunk; ++j) v[j] = (j < (int)left) ? next_output<W, FORM, MAP>(st, rej, p) : 0ull;
     }
     const uint32_t tile = tile0 + (chunk_idx % NBUF) * kTileBytes;
     if (lane == 0) bulk_wait_read<NBUF - 1>();
@@ -315,7 +450,7 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
 // Generic store path (any alignment, any per_stream): the warp stages its 32 x 16 tile with a
 // padded row pitch of 17 words and writes it back row by row, 16 lanes per row, so each store
 // instruction covers two 128-byte row segments.
-template <int W, int FORM>
+template <int W, int FORM, int MAP = 0>
 __global__ void __launch_bounds__(256) fill_plain_kernel(const FillParams p) {
   __shared__ uint64_t tiles[8][32 * (kChunk + 1)];
   const int lane = threadIdx.x & 31;
@@ -332,7 +467,7 @@ __global__ void __launch_bounds__(256) fill_plain_kernel(const FillParams p) {
     const int cnt = left >= (uint64_t)kChunk ? kChunk : (int)left;
 #pragma unroll
     for (int j = 0; j < kChunk; ++j)
-      if (j < cnt) tile[lane * (kChunk + 1) + j] = next_output<W, FORM>(st, rej, p);
+      if (j < cnt) tile[lane * (kChunk + 1) + j] = next_output<W, FORM, MAP>(st, rej, p);
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < kChunk; ++i) {

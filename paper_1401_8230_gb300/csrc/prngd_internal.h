@@ -8,6 +8,10 @@
 #include "prngd.h"
 #include "prngd_math.cuh"
 
+namespace prngd {
+struct FillParams;
+}
+
 namespace prngd_host {
 struct BatchEngine;
 struct BatchShape {
@@ -39,7 +43,12 @@ namespace prngd_host {
 int fail(int code, const char* fmt, ...);
 int check_handle_device(prng_ctx* h);
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
-                uint64_t* rejects, cudaStream_t s, bool allow_tma);
+                uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode = 0);
+// Kernels for the Eq. 5 / 1 - z maps and form L (prngd_modes.cu, prngd_modes_fast.cu): `map`
+// is mode & 3; `tmap` is null for the plain store path.
+cudaError_t launch_fill_map(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap, cudaStream_t s);
+cudaError_t launch_fill_map_fast(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap,
+                                 cudaStream_t s);
 int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
 bool device_mapped_host(const void* p, void** dev);
 bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream);

@@ -331,6 +331,182 @@ PRNGD_HD uint64_t medium24_bits(uint32_t u1, uint32_t u2, uint64_t K) {
   return rn_bits_from_scaled96((uint32_t)(I >> 32) + (uint32_t)(mid >> 32), (uint32_t)mid, (uint32_t)low);
 }
 
+// ------------------------------------------------------------------------ Eq. 5 map
+// Eq. 5 (one generator on [0, 1 - k]: Eq. 6) maps an accepted pair to
+//   z' = (1 - k^2) m / (D - 2),   m = n - 1 = (u1 - 1) 2^w + u2 in [0, D - 2],
+// and its complement 1 - z' = ((D - 2) 2^2w - (2^2w - 1) m) / ((D - 2) 2^2w). Both are never
+// dyadic except at m = 0 and m = D - 2 (gcd(2^2w - 1, D - 2) = 1), so rounding to nearest is
+// again "round up iff the round bit is set". E = D - 2 is odd.
+
+// Division constants of E' = (D - 2) << sh (same construction as divconst_for).
+template <int W>
+PRNGD_HD DivConst divconst_eq5_for() {
+  static_assert(W == 32 || W == 24, "compile-time constants exist for w = 32 and w = 24");
+  if constexpr (W == 32) {
+    return DivConst{0xFFFFFFFDFFFFFFFFull, 0x200000005ull, 0};
+  } else {
+    return DivConst{0xFFFFFDFFFFFF0000ull, 0x20000050000ull, 16};
+  }
+}
+
+// q = floor((u1 2^64 + u0) / d), r = the remainder, for u1 < d and d normalised (Moller-Granlund
+// 2-by-1 division with reciprocal v).
+PRNGD_HD uint64_t div_2by1(uint64_t u1, uint64_t u0, uint64_t d, uint64_t v, uint64_t& r) {
+  uint64_t q0 = v * u1;
+  uint64_t q1 = umulhi64(v, u1);
+  const uint64_t s0 = q0 + u0;
+  q1 += u1 + (s0 < q0 ? 1u : 0u);
+  q0 = s0;
+  q1 += 1;
+  uint64_t rr = u0 - q1 * d;
+  if (rr > q0) {
+    q1 -= 1;
+    rr += d;
+  }
+  if (rr >= d) {
+    q1 += 1;
+    rr -= d;
+  }
+  r = rr;
+  return q1;
+}
+
+// Double bits of RN(N / E) 2^-scale for a 128-bit N = nhi 2^64 + nlo with 1 <= N / E < 2^64
+// and N / E never a tie (ec: the constants of E' = E << ec.sh). N 2^sh / E' has the same value;
+// the first 2-by-1 division gives its integer part q1 (>= 1), a second one the next 64 bits.
+// The 54-bit integer part of the quotient at its binade is taken from q1:q2 and rounded up iff
+// its last bit is set. Returns 0 for N = 0.
+PRNGD_HD uint64_t rn_bits_ratio128(uint64_t nhi, uint64_t nlo, const DivConst& ec, int scale) {
+  if ((nhi | nlo) == 0) return 0;
+  const uint64_t hi = ec.sh ? (nhi << ec.sh) | (nlo >> (64 - ec.sh)) : nhi;
+  const uint64_t lo = nlo << ec.sh;
+  uint64_t r1, r2;
+  const uint64_t q1 = div_2by1(hi, lo, ec.d_norm, ec.v, r1);  // >= 1
+  const uint64_t q2 = div_2by1(r1, 0, ec.d_norm, ec.v, r2);
+  const int L1 = 64 - clz64(q1);  // bit length of q1, in [1, 64]
+  uint64_t q;                     // 54-bit integer part of the quotient at its binade
+  if (L1 >= 54) {
+    q = q1 >> (L1 - 54);
+  } else {
+    const int t = 54 - L1;  // in [1, 53]
+    q = (q1 << t) | (q2 >> (64 - t));
+  }
+  const uint64_t mant = (q >> 1) + (q & 1);  // in [2^52, 2^53]
+  const int e = L1 - 1 - scale;              // unbiased exponent of the value
+  return ((uint64_t)(e + 1022) << 52) + mant;
+}
+
+// Exact Eq. 5 value bits from the accepted pair (u1, u2) of w-bit draws (w in [2, 32]); ec: the
+// constants of D - 2; one_minus selects 1 - z'.
+PRNGD_HD uint64_t eq5_bits_exact_w(uint32_t u1, uint32_t u2, int w, const DivConst& ec, bool one_minus) {
+  const uint64_t m = ((uint64_t)(u1 - 1u) << w) + u2;
+  const int s2 = 2 * w;  // in [4, 64]
+  // N = (2^2w - 1) m = m 2^2w - m, as 128-bit words
+  uint64_t nhi = (s2 == 64) ? m : (m >> (64 - s2));
+  uint64_t nlo = (s2 == 64) ? 0 : (m << s2);
+  nhi -= (nlo < m) ? 1u : 0u;
+  nlo -= m;
+  if (one_minus) {
+    if (m == 0) return 0x3FF0000000000000ull;  // 1 - 0 = 1 exactly (the quotient would be 2^2w)
+    const uint64_t top = (w == 32) ? 0xFFFFFFFFull : ((1ull << w) - 1u);
+    const uint64_t e = top * top - 2u;  // D - 2
+    const uint64_t ehi = (s2 == 64) ? e : (e >> (64 - s2)), elo = (s2 == 64) ? 0 : (e << s2);
+    const uint64_t lo = elo - nlo;
+    nhi = ehi - nhi - (elo < nlo ? 1u : 0u);
+    nlo = lo;
+  }
+  return rn_bits_ratio128(nhi, nlo, ec, s2);
+}
+template <int W>
+PRNGD_HD uint64_t eq5_bits_exact(uint32_t u1, uint32_t u2, bool one_minus) {
+  return eq5_bits_exact_w(u1, u2, W, divconst_eq5_for<W>(), one_minus);
+}
+
+// Fast path for Eq. 5 at w = 32. With delta = 2^-31 + 2^-64, D - 2 = 2^64 (1 - delta) and
+//   (1 - 2^-64) / (1 - delta) = 1 + 2^-31 + 2^-62 + 1.25 2^-93 + O(2^-124)
+// (the 2^-64 terms cancel), so z' 2^64 = m + 2A + u2 2^-31 + A 2^-30 + tail, A = u1 - 1, with a
+// positive tail below 14 2^-32. With Y = 4A + 2 u2 (35 bits) the integer part is
+//   I5 = A 2^32 + 2A + u2 + (Y >> 32)
+// unless the low word of Y is within 64 of 2^32. The complement 1 - z' of the pair is
+// z'(~u1, ~u2) + 2^-64: its integer part is I5 of the complemented draws plus 1. Needs
+// 2^22 <= A <= 2^32 - 4 (as the Eq. 4 fast path).
+PRNGD_HD uint64_t fast32_eq5_Y(uint32_t u1, uint32_t u2) {
+  return ((uint64_t)(u1 - 1u) << 2) + ((uint64_t)u2 << 1);
+}
+PRNGD_HD bool fast32_eq5_ok(uint32_t u1, uint64_t Y) {
+  return ((uint32_t)(u1 - 0x400001u) < 0xFFBFFFFDu) & ((uint32_t)Y < 0xFFFFFFC0u);
+}
+PRNGD_HD uint64_t fast32_eq5_bits(uint32_t u1, uint32_t u2, uint64_t Y, uint32_t plus) {
+  const uint32_t A = u1 - 1u;
+  const uint64_t L = (uint64_t)A * 2u + (uint64_t)u2 + (Y >> 32) + plus;  // < 2^35
+  const uint32_t ilo = (uint32_t)L;
+  const uint32_t ihi = A + (uint32_t)(L >> 32);  // >= 2^22
+  const uint32_t p = 31u - (uint32_t)clz32(ihi);
+  const uint32_t s = p - 21u;
+  const uint32_t jlo = ilo + (1u << s);
+  const uint32_t jhi = ihi + (jlo < ilo ? 1u : 0u);
+  const uint32_t mlo = funnel_r(jlo, jhi, s + 1u);
+  const uint32_t mhi = (jhi >> (s + 1u)) + ((p + 990u) << 20);
+  return ((uint64_t)mhi << 32) | mlo;
+}
+
+// Medium path for Eq. 5 at w = 32, small values 1 <= A < 2^22 (I5 < 2^54). One more series
+// term: z' 2^96 = I5 2^32 + (Y mod 2^32) + Z 2^-32 + tail with Z = 4 u2 + 10 A (35 bits) and
+// a positive tail below 1.25 u2 2^-61 + 2^-38 < 10.01 2^-32, so
+//   floor(z' 2^96) = I5 2^32 + (Y mod 2^32) + (Z >> 32)
+// unless the low word of Z is within 16 of 2^32. The complement adds 2^-64, i.e. 1 to I5 of
+// the complemented draws (plus = 1).
+PRNGD_HD bool medium32_eq5_ok(uint32_t u1, uint32_t u2) {
+  const uint64_t Z = ((uint64_t)u2 << 2) + 10u * (uint64_t)(u1 - 1u);
+  return ((uint32_t)(u1 - 2u) < 0x3FFFFFu) & ((uint32_t)Z < 0xFFFFFFF0u);  // 1 <= A < 2^22
+}
+// The words t2 t1 t0 of floor(z' 2^96) (of the complement's, with plus = 1).
+PRNGD_HD void medium32_eq5_words(uint32_t u1, uint32_t u2, uint64_t Y, uint32_t plus, uint32_t& t2, uint32_t& t1,
+                                 uint32_t& t0) {
+  const uint64_t A = u1 - 1u;
+  const uint64_t Z = ((uint64_t)u2 << 2) + 10u * A;
+  const uint64_t I = (A << 32) + 2u * A + u2 + (Y >> 32) + plus;
+  const uint64_t low = (uint64_t)(uint32_t)Y + (Z >> 32);
+  const uint64_t mid = (I & 0xFFFFFFFFull) + (low >> 32);
+  t2 = (uint32_t)(I >> 32) + (uint32_t)(mid >> 32);
+  t1 = (uint32_t)mid;
+  t0 = (uint32_t)low;
+}
+PRNGD_HD uint64_t medium32_eq5_bits(uint32_t u1, uint32_t u2, uint64_t Y, uint32_t plus) {
+  uint32_t t2, t1, t0;
+  medium32_eq5_words(u1, u2, Y, plus, t2, t1, t0);
+  return rn_bits_from_scaled96(t2, t1, t0);
+}
+
+// Fast path for Eq. 5 at w = 24. With delta = 2^-23 + 2^-48,
+//   (1 - 2^-48) / (1 - delta) = 1 + 2^-23 + 2^-46 + 1.25 2^-69 + O(2^-92),
+// so with m = A 2^24 + u2,
+//   z' 2^64 = A 2^40 + (u2 + 2A) 2^16 + (2^25 u2 + 2^26 A + 4 u2 + 10 A) 2^-32 + tail,
+// tail positive and below 27 2^-32. With K5 = 2^25 u2 + 2^26 A + 4 u2 + 10 A (< 2^51) the
+// integer part is I5 = A 2^40 + (u2 + 2A) 2^16 + (K5 >> 32) unless the low word of K5 is
+// within 64 of 2^32. The complement adds 2^-48, i.e. 2^16 to I5 of the complemented draws.
+// Needs 2^14 <= A <= 2^24 - 3.
+PRNGD_HD uint64_t fast24_eq5_K(uint32_t u1, uint32_t u2) {
+  const uint64_t A = u1 - 1u;
+  return ((uint64_t)u2 << 25) + (A << 26) + 4u * (uint64_t)u2 + 10u * A;
+}
+PRNGD_HD bool fast24_eq5_ok(uint32_t u1, uint64_t K) {
+  return ((uint32_t)(u1 - 1u - 0x4000u) < 0xFFBFFEu) & ((uint32_t)K < 0xFFFFFFC0u);
+}
+PRNGD_HD uint64_t fast24_eq5_bits(uint32_t u1, uint32_t u2, uint64_t K, uint32_t plus) {
+  const uint32_t A = u1 - 1u;
+  const uint64_t L = ((uint64_t)(u2 + 2u * A) << 16) + (K >> 32) + plus;  // < 2^42
+  const uint32_t ilo = (uint32_t)L;
+  const uint32_t ihi = (A << 8) + (uint32_t)(L >> 32);  // >= 2^22
+  const uint32_t p = 31u - (uint32_t)clz32(ihi);
+  const uint32_t s = p - 21u;
+  const uint32_t jlo = ilo + (1u << s);
+  const uint32_t jhi = ihi + (jlo < ilo ? 1u : 0u);
+  const uint32_t mlo = funnel_r(jlo, jhi, s + 1u);
+  const uint32_t mhi = (jhi >> (s + 1u)) + ((p + 990u) << 20);
+  return ((uint64_t)mhi << 32) | mlo;
+}
+
 // Form C from the form-B bits d: hi = RN32(d) by rounding the 53-bit significand to 24 bits
 // (round half to even; d is dyadic so ties occur), lo = RN32(d - hi) where d - hi = R 2^(e-52)
 // exactly for the signed integer R = (low 29 bits) - 2^29 * (rounded up). Packed as

@@ -1,0 +1,50 @@
+// prngd_modes_fast.cu -- fill kernels for the Eq. 5 and 1 - z maps (Section 2) at w = 32 and
+// w = 24, forms B and C: the pair fast paths of prngd_fill.cuh with the map as a template
+// parameter, TMA tile stores. Separate from prngd.cu so the instantiations compile in parallel.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "prngd_fill.cuh"
+#include "prngd_internal.h"
+
+namespace prngd_host {
+namespace {
+constexpr int kWarpsPerBlock = 8;
+constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * prngd::kTileBytes + 1024;
+
+template <int W, int FORM, int MAP>
+cudaError_t launch_fast(const prngd::FillParams& p, const CUtensorMap* tmap, cudaStream_t s) {
+  const uint64_t warps = (p.n_streams + 31) / 32;
+  const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  auto k = prngd::fill_tma_kernel<W, FORM, 1, MAP>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *tmap);
+  return cudaGetLastError();
+}
+
+template <int W, int FORM>
+cudaError_t launch_map(const prngd::FillParams& p, int map, const CUtensorMap* tmap, cudaStream_t s) {
+  switch (map) {
+    case prngd::kMapEq5: return launch_fast<W, FORM, prngd::kMapEq5>(p, tmap, s);
+    case prngd::kMapOneMinus: return launch_fast<W, FORM, prngd::kMapOneMinus>(p, tmap, s);
+    case prngd::kMapEq5 | prngd::kMapOneMinus:
+      return launch_fast<W, FORM, prngd::kMapEq5 | prngd::kMapOneMinus>(p, tmap, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+cudaError_t launch_fill_map_fast(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap,
+                                 cudaStream_t s) {
+  if (!tmap) return cudaErrorInvalidValue;
+  const bool c = form == PRNG_FORM_C_F32PAIR;
+  if (p.w == 32) return c ? launch_map<32, prngd::kFormC>(p, map, tmap, s) : launch_map<32, prngd::kFormB>(p, map, tmap, s);
+  if (p.w == 24) return c ? launch_map<24, prngd::kFormC>(p, map, tmap, s) : launch_map<24, prngd::kFormB>(p, map, tmap, s);
+  return cudaErrorInvalidValue;
+}
+}  // namespace prngd_host

@@ -14,6 +14,7 @@ double orc_value_rn(uint64_t n, int w);
 uint64_t orc_numerator(uint32_t u1, uint32_t u2, int w);
 int orc_accept(uint32_t u1, int w);
 void orc_value_form_c(uint64_t n, int w, float* hi, float* lo);
+int orc_values_mode(const uint32_t* u1, const uint32_t* u2, uint64_t count, int w, int form, int mode, void* out);
 }
 
 using namespace prngd;
@@ -32,6 +33,16 @@ static DivConst make_dc(int w) {
   dc.v = (uint64_t)(all / dc.d_norm - ((unsigned __int128)1 << 64));
   return dc;
 }
+static DivConst make_dc_eq5(int w) {
+  const uint64_t m = (w == 32) ? 0xFFFFFFFFull : ((1ull << w) - 1);
+  const uint64_t e = m * m - 2;
+  DivConst dc;
+  dc.sh = clz64(e);
+  dc.d_norm = e << dc.sh;
+  const unsigned __int128 all = ~(unsigned __int128)0;
+  dc.v = (uint64_t)(all / dc.d_norm - ((unsigned __int128)1 << 64));
+  return dc;
+}
 static long bad = 0, checked = 0;
 static void expect(uint64_t got, uint64_t want, const char* what, uint32_t a, uint32_t b) {
   ++checked;
@@ -43,7 +54,20 @@ static void expect(uint64_t got, uint64_t want, const char* what, uint32_t a, ui
 }
 static uint64_t want_rn(uint32_t u1, uint32_t u2, int w) { return bits_of(orc_value_rn(orc_numerator(u1, u2, w), w)); }
 
-int main() {
+// "words" mode: for each line "u1 u2 plus" on stdin print the 96-bit words of the Eq. 5
+// medium path (t2 t1 t0), for an exact comparison with big-integer arithmetic.
+static int words_mode() {
+  unsigned long long a, b, c;
+  while (scanf("%llu %llu %llu", &a, &b, &c) == 3) {
+    uint32_t t2, t1, t0;
+    medium32_eq5_words((uint32_t)a, (uint32_t)b, fast32_eq5_Y((uint32_t)a, (uint32_t)b), (uint32_t)c, t2, t1, t0);
+    printf("%u %u %u\n", t2, t1, t0);
+  }
+  return 0;
+}
+
+int main(int argc, char** argv) {
+  if (argc > 1 && strcmp(argv[1], "words") == 0) return words_mode();
   std::mt19937_64 rng(2024);
   // 0. the compile-time division constants equal the ones derived at run time
   {
@@ -131,6 +155,95 @@ int main() {
       const uint64_t want = ((uint64_t)(bl - 1 - 96 + 1022) << 52) + m;
       expect(rn_bits_from_scaled96(t2, t1, t0), want, "scaled96", t2, t1);
     }
+  // 5. Eq. 5 and 1 - z: constants, the exact 128-bit path and the fast paths against the oracle
+  {
+    const DivConst a = make_dc_eq5(32), b = divconst_eq5_for<32>(), c = make_dc_eq5(24), d = divconst_eq5_for<24>();
+    expect(a.d_norm == b.d_norm && a.v == b.v && a.sh == b.sh, 1, "divconst_eq5_32", 32, 0);
+    expect(c.d_norm == d.d_norm && c.v == d.v && c.sh == d.sh, 1, "divconst_eq5_24", 24, 0);
+  }
+  auto want_mode = [](uint32_t u1, uint32_t u2, int w, int mode) {
+    double v;
+    orc_values_mode(&u1, &u2, 1, w, 1, mode, &v);
+    return bits_of(v);
+  };
+  for (int w : {32, 24}) {
+    const uint32_t top = (w == 32) ? 0xFFFFFFFFu : 0xFFFFFFu;
+    for (int i = 0; i < 300000; ++i) {
+      uint32_t u1 = 1u + (uint32_t)(rng() % (top - 1u)), u2 = (uint32_t)rng() & top;
+      if (i < 64) {  // end points, small and large values
+        const uint32_t e1[8] = {1u, 1u, 2u, top - 1u, top - 1u, top - 2u, 3u, top / 2u};
+        u1 = e1[i & 7];
+        u2 = (i >> 3) & 1 ? top : (uint32_t)(i >> 4);
+      } else if (i % 3 == 0) {
+        u1 = 1u + (uint32_t)(rng() % ((w == 32) ? (1u << 23) : (1u << 15)));  // small A
+      }
+      for (int om = 0; om < 2; ++om) {
+        const uint64_t want = want_mode(u1, u2, w, 1 | (om << 1));
+        const uint64_t ex = (w == 32) ? eq5_bits_exact<32>(u1, u2, om) : eq5_bits_exact<24>(u1, u2, om);
+        expect(ex, want, om ? "eq5 exact 1-z" : "eq5 exact", u1, u2);
+        const uint32_t a1 = om ? (top - u1) : u1, a2 = om ? (top - u2) : u2;  // complemented draws
+        if (w == 32) {
+          const uint64_t Y = fast32_eq5_Y(a1, a2);
+          if (fast32_eq5_ok(a1, Y)) expect(fast32_eq5_bits(a1, a2, Y, om), want, "fast32_eq5", u1, u2);
+        } else {
+          const uint64_t K = fast24_eq5_K(a1, a2);
+          if (fast24_eq5_ok(a1, K)) expect(fast24_eq5_bits(a1, a2, K, om ? 0x10000u : 0u), want, "fast24_eq5", u1, u2);
+        }
+      }
+      // Eq. 4 complement: the Eq. 4 arithmetic on the complemented draws
+      const uint64_t want_c = want_mode(u1, u2, w, 2);
+      expect(rn_bits_exact(numerator(top - u1, top - u2, w), make_dc(w)), want_c, "eq4 1-z", u1, u2);
+    }
+  }
+  // fast32_eq5 near the low-word boundary of Y = 4A + 2 u2, both maps
+  for (int it = 0; it < 200000; ++it) {
+    const uint32_t u1 = 0x400001u + (uint32_t)(rng() % 0xFFB00000u);
+    const int64_t A = (int64_t)u1 - 1;
+    for (int dd = -80; dd < 8; dd += 2) {
+      const int64_t target = ((int64_t)(1 + rng() % 4) << 32) + dd;
+      const int64_t num = target - 4 * A;
+      if (num < 0 || (num & 1) || num / 2 > 0xFFFFFFFFll) continue;
+      const uint32_t u2 = (uint32_t)(num / 2);
+      const uint64_t Y = fast32_eq5_Y(u1, u2);
+      if (!fast32_eq5_ok(u1, Y)) continue;
+      expect(fast32_eq5_bits(u1, u2, Y, 0), want_mode(u1, u2, 32, 1), "fast32_eq5 edge", u1, u2);
+      expect(fast32_eq5_bits(u1, u2, Y, 1), want_mode(~u1, ~u2, 32, 3), "fast32_eq5 edge 1-z", u1, u2);
+    }
+  }
+  // medium32_eq5: every small u1 class with random u2, and u2 near the low-word boundary of Z
+  for (int it = 0; it < 400000; ++it) {
+    const uint32_t u1 = 2u + (uint32_t)(rng() % ((1u << 22) - 1u));
+    uint32_t u2 = (uint32_t)rng();
+    if (it & 1) {  // Z = 4 u2 + 10 A near k 2^32
+      const int64_t target = ((int64_t)(1 + rng() % 3) << 32) - (int64_t)(rng() % 24);
+      const int64_t num = target - 10 * ((int64_t)u1 - 1);
+      if (num < 0 || (num & 3) || num / 4 > 0xFFFFFFFFll) continue;
+      u2 = (uint32_t)(num / 4);
+    }
+    if (!medium32_eq5_ok(u1, u2)) continue;
+    const uint64_t Y = fast32_eq5_Y(u1, u2);
+    expect(medium32_eq5_bits(u1, u2, Y, 0), want_mode(u1, u2, 32, 1), "medium32_eq5", u1, u2);
+    expect(medium32_eq5_bits(u1, u2, Y, 1), want_mode(~u1, ~u2, 32, 3), "medium32_eq5 1-z", u1, u2);
+  }
+  // fast24_eq5 near the low-word boundary of K5 = (2^25 + 4) u2 + (2^26 + 10) A: solve for u2
+  // modulo 2^30 ((2^23 + 1) is odd) and keep the solutions below 2^24
+  for (int it = 0; it < 4000000; ++it) {
+    const uint32_t u1 = 0x4001u + (uint32_t)(rng() % 0xFFB000u);
+    const uint64_t A = u1 - 1u;
+    const int64_t dd = -80 + (int64_t)(rng() % 88);
+    const uint32_t target = (uint32_t)((int64_t)0x100000000ll + dd);
+    const uint32_t rest = target - (uint32_t)(((uint64_t)1 << 26) * A + 10u * A);
+    if (rest & 3u) continue;
+    uint32_t inv = 1u;  // inverse of 2^23 + 1 modulo 2^30 by Newton iteration
+    for (int j = 0; j < 5; ++j) inv *= 2u - ((1u << 23) + 1u) * inv;
+    const uint32_t u2 = ((rest >> 2) * inv) & ((1u << 30) - 1u);
+    if (u2 > 0xFFFFFFu) continue;
+    const uint64_t K = fast24_eq5_K(u1, u2);
+    if (!fast24_eq5_ok(u1, K)) continue;
+    expect(fast24_eq5_bits(u1, u2, K, 0), want_mode(u1, u2, 24, 1), "fast24_eq5 edge", u1, u2);
+    expect(fast24_eq5_bits(u1, u2, K, 0x10000u), want_mode(0xFFFFFFu - u1, 0xFFFFFFu - u2, 24, 3),
+           "fast24_eq5 edge 1-z", u1, u2);
+  }
   printf("checked %ld bad %ld\n", checked, bad);
   return bad != 0;
 }

@@ -11,7 +11,7 @@ from conftest import ROOT
 import oracle
 
 
-def test_device_arithmetic_matches_oracle_on_edge_cases(tmp_path):
+def build_check(tmp_path):
     gxx = shutil.which("g++")
     if not gxx:
         pytest.skip("g++ not available")
@@ -21,6 +21,50 @@ def test_device_arithmetic_matches_oracle_on_edge_cases(tmp_path):
     subprocess.run([gxx, "-std=c++17", "-O2", "-ffp-contract=off",
                     "-I" + os.path.join(ROOT, "paper_1401_8230_gb300", "csrc"),
                     os.path.join(ROOT, "tests", "host", "math_check.cpp"), str(orc), "-o", str(exe), "-lm"], check=True)
+    return exe
+
+
+def test_device_arithmetic_matches_oracle_on_edge_cases(tmp_path):
+    exe = build_check(tmp_path)
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:]
     assert "bad 0" in out.stdout
+
+
+def test_eq5_medium_path_words_are_the_exact_floor(tmp_path):
+    """The Eq. 5 medium path's 96-bit value is floor(z' 2^96) exactly (z' = (1 - 2^-64) m /
+    (D - 2), m = (u1 - 1) 2^32 + u2; for the complement, 1 - z' of the pair, from the
+    complemented draws with plus = 1), checked with Python big integers on random small u1
+    and on u2 placing the low word of 4 u2 + 10 A next to a multiple of 2^32."""
+    import random
+    exe = build_check(tmp_path)
+    rng = random.Random(5)
+    D2 = (2**32 - 1) ** 2 - 2
+    cases = []
+    while len(cases) < 20000:
+        u1 = rng.randrange(2, 2**22 + 1)
+        if len(cases) % 2:
+            A = u1 - 1
+            target = rng.randrange(1, 4) * 2**32 - rng.randrange(17, 80)
+            num = target - 10 * A
+            if num < 0 or num % 4 or num // 4 >= 2**32:
+                continue
+            u2 = num // 4
+        else:
+            u2 = rng.randrange(0, 2**32)
+        A = u1 - 1
+        if (4 * u2 + 10 * A) % 2**32 >= 2**32 - 16:
+            continue  # outside the medium path
+        cases.append((u1, u2, rng.randrange(2)))
+    inp = "".join(f"{a} {b} {c}\n" for a, b, c in cases)
+    out = subprocess.run([str(exe), "words"], input=inp, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0
+    for (u1, u2, plus), line in zip(cases, out.stdout.split("\n")):
+        t2, t1, t0 = (int(v) for v in line.split())
+        got = (t2 << 64) | (t1 << 32) | t0
+        m = (u1 - 1) * 2**32 + u2
+        if plus:  # the pair is the complement's draws: 1 - z'(~u1, ~u2) = z'(u1, u2) + 2^-64
+            want = ((2**64 - 1) * m * 2**96 + D2 * 2**96) // (D2 * 2**64)
+        else:
+            want = (2**64 - 1) * m * 2**96 // (D2 * 2**64)
+        assert got == want, (u1, u2, plus)
