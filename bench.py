@@ -368,6 +368,15 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
         fn()
         ms = sum(time_calls(torch, fn, reps, stream)) / reps
         res[name] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak}
+    # a few long streams: 64 streams x 2^24 outputs (the same 2^30 outputs), cut into pieces by
+    # jump-ahead so that they fill the GPU (prng_fill_split, automatic piece count)
+    gl = P.Generator(SEED, 64, W)
+    fn = lambda: gl.fill_split(out, n // 64, P.FORM_B_INTBITS, 0, 0, None, stream)  # noqa: E731
+    fn()
+    ms = sum(time_calls(torch, fn, reps, stream)) / reps
+    res["w32_split_64_streams_formB"] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak,
+                                         "note": "64 streams x 2^24 outputs, jump-ahead pieces"}
+    gl.close()
     g24 = P.Generator(SEED, N_STREAMS, 24)
     for name, form in [("w24_formB_intbits", P.FORM_B_INTBITS), ("w24_formA_fp64", P.FORM_A_FP64)]:
         fn = lambda form=form: g24.fill_f64(out, PER_STREAM, form, None, stream)  # noqa: E731

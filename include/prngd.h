@@ -134,6 +134,31 @@ int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mod
                    void* cuda_stream);
 
 /*
+ * prng_skip -- advance every stream of the handle by `draws` base draws (2 per attempt under
+ * the pair rule), as if that many draws had been made and discarded. xorshift128 is linear
+ * over GF(2), so the jump is g(T) applied to each state with g = x^draws mod P, P the
+ * characteristic polynomial of the generator's step T: the cost does not depend on `draws`.
+ * Asynchronous on cuda_stream. Errors: PRNG_EINVAL (null handle), PRNG_ECUDA.
+ */
+int prng_skip(prng_t h, uint64_t draws, void* cuda_stream);
+
+/*
+ * prng_fill_split -- the outputs of prng_fill_mode (same values, same reject counts, same
+ * state afterwards), computed with each stream cut into `segments` pieces that run in
+ * parallel, so that a few long streams fill the GPU. Under the pair rule (Section 2) attempt a
+ * of a stream always uses draws 2a and 2a + 1, so piece j starts from the state jumped ahead by
+ * 2 j (per_stream / segments) draws; the outputs it owns are shifted back by the rejects of the
+ * pieces before it (rare: 2/2^w per attempt), which the call resolves on the device.
+ * segments: a power of two (<= 2^23) dividing per_stream, or 0 to let the library choose
+ * (1 means no split). The single-redraw rule of Algorithm 1 has no fixed attempt boundaries and
+ * is refused. Scratch (28 bytes per piece) is kept with the handle.
+ * Errors: PRNG_EINVAL (as prng_fill_mode; PRNG_MODE_SINGLE_REDRAW; bad segments),
+ * PRNG_ENOMEM, PRNG_ECUDA.
+ */
+int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mode, uint32_t segments,
+                    uint64_t* d_rejects, void* cuda_stream);
+
+/*
  * prng_fill_f64_host -- end-to-end fill into HOST memory: the same values as prng_fill_f64
  * (the streams advance identically) into `host_out` (n_streams * per_stream doubles). If
  * host_out is pinned (page-locked and mapped for the device), one kernel writes it directly

@@ -53,6 +53,8 @@ def lib() -> ctypes.CDLL:
             L.orc_stream_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _U32P]
             L.orc_xorshift128_next.restype = ctypes.c_uint32
             L.orc_xorshift128_next.argtypes = [_U32P]
+            L.orc_skip.restype = None
+            L.orc_skip.argtypes = [_U32P, ctypes.c_uint64]
             L.orc_stream_raw.restype = None
             L.orc_stream_raw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, _U32P]
             L.orc_accept.restype = ctypes.c_int
@@ -122,6 +124,13 @@ def xorshift128_outputs(state, count: int) -> np.ndarray:
     p = st.ctypes.data_as(_U32P)
     L = lib()
     return np.array([L.orc_xorshift128_next(p) for _ in range(count)], dtype=np.uint32)
+
+
+def skip(state, draws: int) -> np.ndarray:
+    """The state after `draws` steps of the generator."""
+    st = np.array(state, dtype=np.uint32).copy()
+    lib().orc_skip(st.ctypes.data_as(_U32P), draws)
+    return st
 
 
 def stream_raw(seed: int, stream: int, count: int) -> np.ndarray:

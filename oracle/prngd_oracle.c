@@ -85,6 +85,11 @@ uint32_t orc_draw(uint32_t st[4], int w) {
     return (w == 32) ? r : (r >> (32 - w));
 }
 
+/* The state after `draws` more draws: the generator stepped that many times. */
+void orc_skip(uint32_t st[4], uint64_t draws) {
+    for (uint64_t i = 0; i < draws; ++i) orc_xorshift128_next(st);
+}
+
 /* First `count` raw 32-bit outputs of one stream. */
 void orc_stream_raw(uint64_t seed, uint64_t stream, uint64_t count, uint32_t* out) {
     uint32_t st[4];

@@ -51,6 +51,8 @@ _SIGNATURES = {
     "prng_fill_f64": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fill_f32pair": (_i32, [_P, _vp, _u64, _vp, _vp]),
     "prng_fill_mode": (_i32, [_P, _vp, _u64, ctypes.c_int, ctypes.c_int, _vp, _vp]),
+    "prng_fill_split": (_i32, [_P, _vp, _u64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _vp, _vp]),
+    "prng_skip": (_i32, [_P, _u64, _vp]),
     "prng_fill_f64_host": (_i32, [_P, _vp, _u64, _i32, _vp]),
     "prng_fill_f64_host_noalloc": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
@@ -171,6 +173,15 @@ def prng_fill_f32pair(h: int, out, per_stream: int, rejects=None, stream=None) -
 
 def prng_fill_mode(h: int, out, per_stream: int, form: int, mode: int, rejects=None, stream=None) -> None:
     _check(lib().prng_fill_mode(h, _ptr(out), per_stream, form, mode, _ptr(rejects), _stream(stream)))
+
+
+def prng_fill_split(h: int, out, per_stream: int, form: int, mode: int = 0, segments: int = 0, rejects=None,
+                    stream=None) -> None:
+    _check(lib().prng_fill_split(h, _ptr(out), per_stream, form, mode, segments, _ptr(rejects), _stream(stream)))
+
+
+def prng_skip(h: int, draws: int, stream=None) -> None:
+    _check(lib().prng_skip(h, draws, _stream(stream)))
 
 
 def prng_fill_f64_host(h: int, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None) -> None:
@@ -328,6 +339,14 @@ class Generator:
     def fill_mode(self, out, per_stream: int, form: int, mode: int, rejects=None, stream=None):
         prng_fill_mode(self.h, out, per_stream, form, mode, rejects, stream)
         return out
+
+    def fill_split(self, out, per_stream: int, form: int = FORM_B_INTBITS, mode: int = 0, segments: int = 0,
+                   rejects=None, stream=None):
+        prng_fill_split(self.h, out, per_stream, form, mode, segments, rejects, stream)
+        return out
+
+    def skip(self, draws: int, stream=None) -> None:
+        prng_skip(self.h, draws, stream)
 
     def fill_f64_host(self, out, per_stream: int, form: int = FORM_B_INTBITS, rejects=None):
         prng_fill_f64_host(self.h, out, per_stream, form, rejects)

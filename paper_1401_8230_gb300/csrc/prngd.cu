@@ -65,7 +65,7 @@ DivConst make_divconst_eq5(int w) {
 // The constants the map kernels take: C5 = RN((2^2w - 1) / ((D - 2) 2^2w)) for form A under
 // Eq. 5, and form L's folded constants, each one IEEE double operation as Algorithm 1 (Eq. 4)
 // or Eq. 6 writes them (volatile: no contraction, one rounding per operation).
-static void set_mode_constants(FillParams& p, int w, int mode) {
+void set_mode_constants(FillParams& p, int w, int mode) {
   p.single = (mode & PRNG_MODE_SINGLE_REDRAW) ? 1u : 0u;
   p.ec = make_divconst_eq5(w);
   const int s2 = 2 * w;
@@ -288,6 +288,7 @@ int prng_destroy(prng_t h) {
   cudaDeviceSynchronize();
   release_batch(h);
   release_aux(h);
+  release_split(h);
   cudaFree(h->d_state);
   delete h;
   return PRNG_OK;

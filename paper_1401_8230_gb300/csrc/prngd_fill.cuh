@@ -124,6 +124,31 @@ __device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, cons
   }
 }
 
+// The output of an accepted pair by the fastest valid path: at w = 32, forms B and C, the fast
+// path, then the medium path for small values, else the exact conversion.
+template <int W, int FORM, int MAP>
+__device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, const FillParams& p) {
+  if constexpr (W == 32 && (FORM == kFormB || FORM == kFormC)) {
+    constexpr bool kComp = (MAP & kMapOneMinus) != 0;
+    const uint32_t a1 = kComp ? ~u1 : u1, a2 = kComp ? ~u2 : u2;
+    uint64_t bits;
+    if constexpr ((MAP & kMapEq5) != 0) {
+      const uint64_t Y = fast32_eq5_Y(a1, a2);
+      if (fast32_eq5_ok(a1, Y)) bits = fast32_eq5_bits(a1, a2, Y, kComp ? 1u : 0u);
+      else if (medium32_eq5_ok(a1, a2)) bits = medium32_eq5_bits(a1, a2, Y, kComp ? 1u : 0u);
+      else return convert_exact<W, FORM, MAP>(u1, u2, p);
+    } else {
+      const uint64_t X = fast32_X(a1, a2);
+      if (fast32_ok(a1, X)) bits = fast32_bits(a1, a2, X);
+      else if (medium32_ok(a1, X, a2)) bits = medium32_bits(a1, a2, X);
+      else return convert_exact<W, FORM, MAP>(u1, u2, p);
+    }
+    return FORM == kFormC ? f32pair_from_bits(bits) : bits;
+  } else {
+    return convert_exact<W, FORM, MAP>(u1, u2, p);
+  }
+}
+
 // The slow path of one output: redraw rejected attempts in order, then convert exactly. Only
 // entered for a reject (probability 2^(1-w)), for small values (probability ~2^-10) and for
 // the rare values near a rounding boundary of the fast paths.

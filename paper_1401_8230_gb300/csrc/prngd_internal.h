@@ -37,6 +37,11 @@ struct prng_ctx {
   cudaStream_t io_stream[2] = {nullptr, nullptr};
   // batched requests (created on first use)
   prngd_host::BatchEngine* batch = nullptr;
+  // split-fill scratch (grown on demand)
+  void* split_mem = nullptr;
+  size_t split_bytes = 0;
+  uint64_t split_table_seg = 0;     // segment length the jump table in the scratch was built for
+  void* split_table_mem = nullptr;  // where that table lives
 };
 
 namespace prngd_host {
@@ -53,6 +58,9 @@ int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint
 bool device_mapped_host(const void* p, void** dev);
 bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream);
 void release_aux(prng_ctx* h);
+void release_split(prng_ctx* h);
+// Mode-dependent constants of FillParams (reject rule, Eq. 5 division constants, form L).
+void set_mode_constants(prngd::FillParams& p, int w, int mode);
 void release_batch(prng_ctx* h);
 BatchShape default_batch_shape(int num_sms);
 int set_batch_shape(prng_ctx* h, const BatchShape& sh);

@@ -140,6 +140,25 @@ PRNGD_HD void xs_prev(XorShift128& s) {
   s.x = x0;
 }
 
+// T^J s for g = x^J mod P, g given as four 32-bit words (bit i of the polynomial = bit i%32 of
+// word i/32): the sum of T^i s over the set bits of g.
+PRNGD_HD XorShift128 apply_poly(const uint32_t g[4], XorShift128 s) {
+  XorShift128 acc{0u, 0u, 0u, 0u};
+  for (int word = 0; word < 4; ++word) {
+    uint32_t bits = g[word];
+    for (int b = 0; b < 32; ++b) {
+      const uint32_t m = 0u - (bits & 1u);  // all ones when the coefficient is set
+      acc.x ^= s.x & m;
+      acc.y ^= s.y & m;
+      acc.z ^= s.z & m;
+      acc.w ^= s.w & m;
+      bits >>= 1;
+      xs_next(s);
+    }
+  }
+  return acc;
+}
+
 // A w-bit base draw: the top w bits of the 32-bit output (x = u 2^-w).
 template <int W>
 PRNGD_HD uint32_t draw(XorShift128& s, int w_rt) {
