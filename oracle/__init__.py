@@ -53,6 +53,15 @@ def lib() -> ctypes.CDLL:
             L.orc_stream_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _U32P]
             L.orc_xorshift128_next.restype = ctypes.c_uint32
             L.orc_xorshift128_next.argtypes = [_U32P]
+            L.orc_mrg32k3a_next.restype = ctypes.c_uint32
+            L.orc_mrg32k3a_next.argtypes = [_U32P]
+            L.orc_mrg_stream_seed.restype = None
+            L.orc_mrg_stream_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint64, _U32P]
+            L.orc_mrg_denominator.restype = ctypes.c_uint64
+            L.orc_mrg_denominator.argtypes = []
+            L.orc_fill_mrg.restype = ctypes.c_int
+            L.orc_fill_mrg.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                       ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_skip.restype = None
             L.orc_skip.argtypes = [_U32P, ctypes.c_uint64]
             L.orc_stream_raw.restype = None
@@ -131,6 +140,37 @@ def skip(state, draws: int) -> np.ndarray:
     st = np.array(state, dtype=np.uint32).copy()
     lib().orc_skip(st.ctypes.data_as(_U32P), draws)
     return st
+
+
+MRG_M1, MRG_M2 = 4294967087, 4294944443
+
+
+def mrg_stream_seed(seed: int, stream: int) -> np.ndarray:
+    st = np.zeros(6, dtype=np.uint32)
+    lib().orc_mrg_stream_seed(seed, stream, st.ctypes.data_as(_U32P))
+    return st
+
+
+def mrg_outputs(state, count: int):
+    """`count` MRG32k3a outputs z in [1, m1] continued from `state`, and the state after them."""
+    st = np.array(state, dtype=np.uint32).copy()
+    p = st.ctypes.data_as(_U32P)
+    L = lib()
+    return np.array([L.orc_mrg32k3a_next(p) for _ in range(count)], dtype=np.uint64), st
+
+
+def mrg_denominator() -> int:
+    return int(lib().orc_mrg_denominator())
+
+
+def fill_mrg(seed: int, first_stream: int, n_streams: int, per_stream: int, form: int):
+    """Stream-major fill over MRG32k3a streams; returns (out, rejects per stream)."""
+    out = _out_array(n_streams * per_stream, form)
+    rej = np.zeros(n_streams, dtype=np.uint64)
+    rc = lib().orc_fill_mrg(seed, first_stream, n_streams, per_stream, form, _ptr(out), _ptr(rej))
+    if rc != 0:
+        raise ValueError(f"orc_fill_mrg rc={rc}")
+    return out, rej
 
 
 def stream_raw(seed: int, stream: int, count: int) -> np.ndarray:

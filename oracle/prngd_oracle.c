@@ -97,6 +97,52 @@ void orc_stream_raw(uint64_t seed, uint64_t stream, uint64_t count, uint32_t* ou
     for (uint64_t i = 0; i < count; ++i) out[i] = orc_xorshift128_next(st);
 }
 
+/* L'Ecuyer's MRG32k3a ("Good parameters and implementations for combined multiple recursive
+ * random number generators", Operations Research 47(1), 1999), one of the generators Section 2
+ * recommends: two order-3 recurrences
+ *     x1_n = (1403580 x1_{n-2} - 810728 x1_{n-3}) mod m1,   m1 = 2^32 - 209,
+ *     x2_n = (527612 x2_{n-1} - 1370589 x2_{n-3}) mod m2,   m2 = 2^32 - 22853,
+ * combined as z_n = (x1_n - x2_n) mod m1, with z = 0 reported as m1 (so z is in [1, m1]).
+ * State st = (x1_{n-3}, x1_{n-2}, x1_{n-1}, x2_{n-3}, x2_{n-2}, x2_{n-1}). Exact 64-bit integer
+ * arithmetic. Returns z. */
+#define ORC_MRG_M1 4294967087ull
+#define ORC_MRG_M2 4294944443ull
+uint32_t orc_mrg32k3a_next(uint32_t st[6]) {
+    int64_t p1 = (int64_t)(1403580ll * st[1]) - (int64_t)(810728ll * st[0]);
+    p1 %= (int64_t)ORC_MRG_M1;
+    if (p1 < 0) p1 += (int64_t)ORC_MRG_M1;
+    int64_t p2 = (int64_t)(527612ll * st[5]) - (int64_t)(1370589ll * st[3]);
+    p2 %= (int64_t)ORC_MRG_M2;
+    if (p2 < 0) p2 += (int64_t)ORC_MRG_M2;
+    st[0] = st[1];
+    st[1] = st[2];
+    st[2] = (uint32_t)p1;
+    st[3] = st[4];
+    st[4] = st[5];
+    st[5] = (uint32_t)p2;
+    int64_t z = p1 - p2;
+    if (z <= 0) z += (int64_t)ORC_MRG_M1;
+    return (uint32_t)z;
+}
+
+/* MRG32k3a stream seeding (the paper is silent): stream s takes splitmix64 outputs 3s, 3s+1 and
+ * 3s+2 of `seed`, split into six 32-bit words w0..w5 (low word first); x1 state = w0..w2 mod m1,
+ * x2 state = w3..w5 mod m2; a component that comes out all zero gets 1 as its first word. */
+void orc_mrg_stream_seed(uint64_t seed, uint64_t stream, uint32_t st[6]) {
+    uint32_t w[6];
+    for (int i = 0; i < 3; ++i) {
+        uint64_t o = orc_splitmix64_output(seed, 3 * stream + (uint64_t)i);
+        w[2 * i] = (uint32_t)o;
+        w[2 * i + 1] = (uint32_t)(o >> 32);
+    }
+    for (int i = 0; i < 3; ++i) {
+        st[i] = (uint32_t)(w[i] % ORC_MRG_M1);
+        st[3 + i] = (uint32_t)(w[3 + i] % ORC_MRG_M2);
+    }
+    if (!st[0] && !st[1] && !st[2]) st[0] = 1;
+    if (!st[3] && !st[4] && !st[5]) st[3] = 1;
+}
+
 /* ------------------------------------------------------------------------------------------
  * The method, Section 2.
  * ---------------------------------------------------------------------------------------- */
@@ -490,6 +536,57 @@ int orc_enumerate_pairs(int w, uint8_t* accept, uint64_t* n) {
             accept[i] = (uint8_t)orc_accept((uint32_t)u1, w);
             n[i] = accept[i] ? orc_numerator((uint32_t)u1, (uint32_t)u2, w) : 0;
         }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * The method over MRG32k3a draws. The base PRN of the method is a grid of M points with step
+ * k = 1/M; MRG32k3a's z in [1, m1] is read as the draw u = z - 1 on the grid of M = m1 points.
+ * Everything of Section 2 then holds with 2^w replaced by M: accept u1 not in {0, M - 1},
+ * z' = n / D with n = u1 M + u2 - (M - 1) and D = (M - 1)^2 (< 2^64).
+ * ---------------------------------------------------------------------------------------- */
+uint64_t orc_mrg_denominator(void) { return (ORC_MRG_M1 - 1) * (ORC_MRG_M1 - 1); }
+
+/* Stream-major fill (forms A, B, C, N) with the pair rule, as orc_fill. */
+int orc_fill_mrg(uint64_t seed, uint64_t first_stream, uint64_t n_streams, uint64_t per_stream, int form,
+                 void* out, uint64_t* rejects) {
+    if (form < 0 || form > 3 || (!out && n_streams && per_stream)) return ORC_EINVAL;
+    const uint64_t M = ORC_MRG_M1, D = orc_mrg_denominator();
+    volatile double c = orc_rn_ratio(1, D);
+    for (uint64_t j = 0; j < n_streams; ++j) {
+        uint32_t st[6];
+        uint64_t rj = 0;
+        orc_mrg_stream_seed(seed, first_stream + j, st);
+        for (uint64_t i = 0; i < per_stream; ++i) {
+            uint64_t u1, u2;
+            for (;;) {
+                u1 = orc_mrg32k3a_next(st) - 1u;
+                u2 = orc_mrg32k3a_next(st) - 1u;
+                if (u1 != 0 && u1 != M - 1) break;
+                ++rj;
+            }
+            const uint64_t n = u1 * M + u2 - (M - 1);
+            const uint64_t k = j * per_stream + i;
+            switch (form) {
+                case ORC_FORM_A: {
+                    volatile double dn = (double)n;
+                    ((double*)out)[k] = dn * c;
+                    break;
+                }
+                case ORC_FORM_B: ((double*)out)[k] = orc_rn_ratio(n, D); break;
+                case ORC_FORM_C: {
+                    double d = orc_rn_ratio(n, D);
+                    volatile float h = (float)d;
+                    volatile double rest = d - (double)h;
+                    ((float*)out)[2 * k] = h;
+                    ((float*)out)[2 * k + 1] = (float)rest;
+                    break;
+                }
+                default: ((uint64_t*)out)[k] = n; break;
+            }
+        }
+        if (rejects) rejects[j] = rj;
+    }
     return ORC_OK;
 }
 
