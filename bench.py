@@ -377,6 +377,14 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
     res["w32_split_64_streams_formB"] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak,
                                          "note": "64 streams x 2^24 outputs, jump-ahead pieces"}
     gl.close()
+    # MRG32k3a base streams (Section 2's recommended generators), same sizes, form B
+    gm = P.Generator(SEED, N_STREAMS, generator=P.GEN_MRG32K3A)
+    fn = lambda: gm.fill_f64(out, PER_STREAM, P.FORM_B_INTBITS, None, stream)  # noqa: E731
+    fn()
+    ms = sum(time_calls(torch, fn, reps, stream)) / reps
+    res["mrg32k3a_formB"] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak,
+                             "note": "2^20 MRG32k3a streams x 1024, M = m1 grid, exact division"}
+    gm.close()
     g24 = P.Generator(SEED, N_STREAMS, 24)
     for name, form in [("w24_formB_intbits", P.FORM_B_INTBITS), ("w24_formA_fp64", P.FORM_A_FP64)]:
         fn = lambda form=form: g24.fill_f64(out, PER_STREAM, form, None, stream)  # noqa: E731

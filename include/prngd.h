@@ -65,6 +65,10 @@ extern "C" {
 
 typedef struct prng_ctx* prng_t;
 
+/* Base generators of a handle's streams. */
+#define PRNG_GEN_XORSHIFT128 0 /* Marsaglia's xor128 (prng_create): every entry point            */
+#define PRNG_GEN_MRG32K3A 1    /* L'Ecuyer's MRG32k3a (prng_create_mrg32k3a): the fills only     */
+
 /* Human-readable message for the calling thread's last failed call ("" if none). */
 const char* prng_last_error(void);
 
@@ -83,6 +87,24 @@ int prng_version(void);
  */
 int prng_create(prng_t* out, uint64_t seed, uint64_t n_streams, int w, double a0, double a,
                 double b0, double b);
+
+/*
+ * prng_create_mrg32k3a -- streams of L'Ecuyer's MRG32k3a (Operations Research 47(1), 1999), one
+ * of the base generators Section 2 recommends. Its output z in [1, m1] (m1 = 2^32 - 209) is the
+ * draw u = z - 1 on a grid of M = m1 points with step k = 1/M, and Section 2 holds with 2^w
+ * replaced by M: u1 in {0, M - 1} is rejected (pair rule) and z' = n/D with
+ * n = u1 M + u2 - (M - 1), D = (M - 1)^2. Stream s is seeded from splitmix64 outputs 3s, 3s+1
+ * and 3s+2 of `seed` (six 32-bit words, low first, reduced modulo m1 and m2; an all-zero
+ * component gets 1 as its first word). 32 bytes of device state per stream.
+ * Such a handle takes prng_fill_f64, prng_fill_f32pair, prng_fill_mode (mode 0, forms A, B, C),
+ * prng_fill_f64_host(_noalloc) and prng_state_*; the entry points built on xorshift128's
+ * structure (fused statistics, batches, serving, skip, split) answer PRNG_EINVAL.
+ * Errors: PRNG_EINVAL (out == NULL, n_streams == 0 or > 2^32), PRNG_ENOMEM, PRNG_ECUDA.
+ */
+int prng_create_mrg32k3a(prng_t* out, uint64_t seed, uint64_t n_streams);
+
+/* PRNG_GEN_* of a handle's streams; -1 for NULL. */
+int prng_generator(prng_t h);
 
 /* Release the handle and its device memory (synchronises the device first). NULL is a no-op. */
 int prng_destroy(prng_t h);
@@ -351,7 +373,7 @@ int prng_server_run_trace(prng_server_t s, const prng_trace_item* items, uint64_
 
 /*
  * State checkpoint: each stream's state is 16 bytes (xorshift128 words x, y, z, w).
- * prng_state_bytes gives n_streams * 16. save copies the device state into host_buf and
+ * prng_state_bytes gives n_streams * 16 (32 for MRG32k3a streams). save copies the device state into host_buf and
  * restore copies it back; both synchronise. A fill after restore reproduces the outputs
  * that followed the save, bit for bit.
  * Errors: PRNG_EINVAL (null pointers, bytes != prng_state_bytes), PRNG_ECUDA.

@@ -10,6 +10,7 @@ from . import build as _build
 PRNG_OK, PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA, PRNG_ETIMEOUT, PRNG_EBUSY, PRNG_ENOTFOUND = range(7)
 FORM_A_FP64, FORM_B_INTBITS, FORM_C_F32PAIR, FORM_L_ALGO1 = 0, 1, 2, 4
 MODE_EQ5, MODE_ONE_MINUS, MODE_SINGLE_REDRAW = 1, 2, 4
+GEN_XORSHIFT128, GEN_MRG32K3A = 0, 1
 REQ_FRESH, REQ_RESIDENT = 0, 1
 MAX_BATCH_REQUESTS = 4096
 
@@ -47,6 +48,8 @@ _SIGNATURES = {
     "prng_version": (_i32, []),
     "prng_create": (_i32, [ctypes.POINTER(_P), _u64, _u64, _i32, _dbl, _dbl, _dbl, _dbl]),
     "prng_destroy": (_i32, [_P]),
+    "prng_create_mrg32k3a": (_i32, [ctypes.POINTER(_P), _u64, _u64]),
+    "prng_generator": (_i32, [_P]),
     "prng_get_info": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(_i32)]),
     "prng_fill_f64": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fill_f32pair": (_i32, [_P, _vp, _u64, _vp, _vp]),
@@ -151,6 +154,16 @@ def prng_create(seed: int, n_streams: int, w: int = 32, a0: float = 0.0, a: floa
     h = _P()
     _check(lib().prng_create(ctypes.byref(h), seed & (2**64 - 1), n_streams, w, a0, a, b0, b))
     return h.value
+
+
+def prng_create_mrg32k3a(seed: int, n_streams: int) -> int:
+    h = _P()
+    _check(lib().prng_create_mrg32k3a(ctypes.byref(h), seed & (2**64 - 1), n_streams))
+    return h.value
+
+
+def prng_generator(h: int) -> int:
+    return int(lib().prng_generator(h))
 
 
 def prng_destroy(h: int) -> None:
@@ -307,9 +320,13 @@ def prng_state_restore(h: int, buf) -> None:
 class Generator:
     """Owning wrapper of a handle; methods forward to the prng_* functions."""
 
-    def __init__(self, seed: int, n_streams: int, w: int = 32, **ranges):
-        self.h = prng_create(seed, n_streams, w, **ranges)
+    def __init__(self, seed: int, n_streams: int, w: int = 32, generator: int = GEN_XORSHIFT128, **ranges):
+        if generator == GEN_MRG32K3A:
+            self.h = prng_create_mrg32k3a(seed, n_streams)
+        else:
+            self.h = prng_create(seed, n_streams, w, **ranges)
         self.n_streams, self.w = prng_get_info(self.h)
+        self.generator = prng_generator(self.h)
 
     def close(self) -> None:
         if self.h:

@@ -181,8 +181,16 @@ bool device_mapped_host(const void* p, void** dev) {
   return true;
 }
 
+int require_xorshift(prng_ctx* h, const char* what) {
+  if (h->gen != PRNG_GEN_XORSHIFT128)
+    return fail(PRNG_EINVAL, "%s is available for xorshift128 streams only", what);
+  return PRNG_OK;
+}
+
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                 uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode) {
+  if (h->gen == PRNG_GEN_MRG32K3A)
+    return launch_fill_mrg(h, state, n_streams, out, per_stream, form, rejects, s, allow_tma, mode);
   if (n_streams == 0 || per_stream == 0) return PRNG_OK;
   if (allow_tma && device_mapped_host(out, nullptr)) allow_tma = false;  // host memory: plain stores only
   FillParams p;
@@ -342,7 +350,9 @@ int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mod
                      true, mode);
 }
 
-size_t prng_state_bytes(prng_t h) { return h ? (size_t)h->n_streams * 16 : 0; }
+size_t prng_state_bytes(prng_t h) {
+  return h ? (size_t)h->n_streams * (h->gen == PRNG_GEN_MRG32K3A ? 32 : 16) : 0;
+}
 
 int prng_state_save(prng_t h, void* host_buf, size_t bytes) {
   if (!h || !host_buf) return fail(PRNG_EINVAL, "null argument");

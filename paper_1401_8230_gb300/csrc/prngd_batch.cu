@@ -472,7 +472,8 @@ extern "C" {
 
 int prng_submit(prng_t h, const prng_request* reqs, int n, uint64_t* ticket, void* cuda_stream) {
   if (!h || !reqs || !ticket) return fail(PRNG_EINVAL, "null argument");
-  int rc = check_handle_device(h);
+  int rc = require_xorshift(h, "prng_submit");
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return submit(h, reqs, n, ticket, (cudaStream_t)cuda_stream);
 }

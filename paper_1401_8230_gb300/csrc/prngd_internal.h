@@ -22,11 +22,13 @@ struct BatchShape {
 }  // namespace prngd_host
 
 struct prng_ctx {
+  int gen = PRNG_GEN_XORSHIFT128;  // base generator of the streams
   int device;
   uint64_t seed;
   uint64_t n_streams;
   int w;
-  uint4* d_state;       // n_streams xorshift128 states, resident between calls
+  uint4* d_state;       // the streams' states, resident between calls: one uint4 per xorshift128
+                        // stream, two per MRG32k3a stream
   prngd::DivConst dc;   // exact-division constants of D = (2^w - 1)^2
   double scale;         // C_w = RN(1/D)
   int num_sms;          // multiprocessors of the handle's device
@@ -59,6 +61,13 @@ bool device_mapped_host(const void* p, void** dev);
 bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream);
 void release_aux(prng_ctx* h);
 void release_split(prng_ctx* h);
+int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
+                    uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode);
+// State of stream s within the handle's state array (uint4 units per stream depend on the generator).
+inline uint4* state_at(prng_ctx* h, uint64_t s) { return h->d_state + (h->gen == PRNG_GEN_MRG32K3A ? 2 * s : s); }
+// PRNG_EINVAL unless the handle's streams are xorshift128 (paths built on its GF(2) structure,
+// its fast conversions or its 16-byte state).
+int require_xorshift(prng_ctx* h, const char* what);
 // Mode-dependent constants of FillParams (reject rule, Eq. 5 division constants, form L).
 void set_mode_constants(prngd::FillParams& p, int w, int mode);
 void release_batch(prng_ctx* h);

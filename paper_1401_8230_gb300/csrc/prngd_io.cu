@@ -90,7 +90,7 @@ int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint
   for (uint64_t s0 = 0; s0 < h->n_streams; s0 += slice, ++k) {
     const uint64_t cnt = (h->n_streams - s0 < slice) ? h->n_streams - s0 : slice;
     const int b = k & 1;
-    int rc = launch_fill(h, h->d_state + s0, cnt, h->d_stage[b], per_stream, form,
+    int rc = launch_fill(h, state_at(h, s0), cnt, h->d_stage[b], per_stream, form,
                          host_rejects ? h->d_rej_stage + s0 : nullptr, h->io_stream[b], true);
     if (rc) return rc;
     e = cudaMemcpyAsync(host_out + s0 * per_stream, h->d_stage[b], (size_t)cnt * row, cudaMemcpyDeviceToHost,

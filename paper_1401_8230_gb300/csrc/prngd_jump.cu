@@ -382,7 +382,8 @@ extern "C" {
 
 int prng_skip(prng_t h, uint64_t draws, void* cuda_stream) {
   if (!h) return fail(PRNG_EINVAL, "null handle");
-  int rc = check_handle_device(h);
+  int rc = require_xorshift(h, "prng_skip");
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return skip_streams(h, draws, (cudaStream_t)cuda_stream);
 }
@@ -398,7 +399,8 @@ int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mo
   if (per_stream == 0) return PRNG_OK;
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
-  int rc = check_handle_device(h);
+  int rc = require_xorshift(h, "prng_fill_split");
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return fill_split(h, d_out, per_stream, form, mode, segments, d_rejects, (cudaStream_t)cuda_stream);
 }

@@ -1,0 +1,233 @@
+// prngd_mrg.cu -- streams of L'Ecuyer's MRG32k3a (Operations Research 47(1), 1999), one of the
+// base generators Section 2 recommends, and the fill over them.
+//
+// Two order-3 recurrences, x1_n = (1403580 x1_{n-2} - 810728 x1_{n-3}) mod m1 and
+// x2_n = (527612 x2_{n-1} - 1370589 x2_{n-3}) mod m2 with m1 = 2^32 - 209, m2 = 2^32 - 22853,
+// combined as z = (x1 - x2) mod m1 in [1, m1] (0 reported as m1). The method reads z as the
+// draw u = z - 1 on a grid of M = m1 points with step k = 1/M, so Section 2 holds with 2^w
+// replaced by M: pairs with u1 in {0, M - 1} are rejected and z' = n / D with
+// n = u1 M + u2 - (M - 1), D = (M - 1)^2 < 2^64, converted exactly (Moller-Granlund division).
+//
+// State: 32 bytes per stream in the handle's state array (two uint4: x1_{n-3}, x1_{n-2},
+// x1_{n-1}, x2_{n-3} | x2_{n-2}, x2_{n-1}, 0, 0), seeded from splitmix64 outputs 3s, 3s+1, 3s+2.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "prngd_fill.cuh"
+#include "prngd_internal.h"
+#include "prngd_mrg.cuh"
+
+namespace prngd {
+
+__device__ __forceinline__ Mrg32k3a mrg_load(const uint4* state, uint64_t s) {
+  const uint4 a = state[2 * s], b = state[2 * s + 1];
+  return Mrg32k3a{a.x, a.y, a.z, a.w, b.x, b.y};
+}
+__device__ __forceinline__ void mrg_store(uint4* state, uint64_t s, const Mrg32k3a& g) {
+  state[2 * s] = make_uint4(g.a0, g.a1, g.a2, g.b0);
+  state[2 * s + 1] = make_uint4(g.b1, g.b2, 0u, 0u);
+}
+
+// Stream s of `seed`: splitmix64 outputs 3s, 3s+1, 3s+2 as six 32-bit words (low word first),
+// reduced modulo m1 (x1 words) and m2 (x2 words); an all-zero component gets 1 as its first word.
+__global__ void mrg_seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
+  const uint64_t s = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  uint32_t w[6];
+  for (int i = 0; i < 3; ++i) {
+    const uint64_t o = splitmix_finalise(seed + (3 * s + (uint64_t)i + 1) * kGoldenGamma);
+    w[2 * i] = (uint32_t)o;
+    w[2 * i + 1] = (uint32_t)(o >> 32);
+  }
+  Mrg32k3a g{w[0] % kMrgM1, w[1] % kMrgM1, w[2] % kMrgM1, w[3] % kMrgM2, w[4] % kMrgM2, w[5] % kMrgM2};
+  if ((g.a0 | g.a1 | g.a2) == 0) g.a0 = 1;
+  if ((g.b0 | g.b1 | g.b2) == 0) g.b0 = 1;
+  mrg_store(state, s, g);
+}
+
+// One output of the method over MRG32k3a draws (pair rule), 8 bytes of form FORM.
+template <int FORM>
+__device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, const FillParams& p) {
+  uint32_t u1, u2;
+  for (;;) {
+    u1 = mrg_next(g) - 1u;
+    u2 = mrg_next(g) - 1u;
+    if (u1 - 1u < kMrgM1 - 2u) break;  // u1 not in {0, M - 1}
+    ++rej;
+  }
+  const uint64_t n = (uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u);
+  if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
+  const uint64_t bits = rn_bits_exact(n, p.dc);
+  return FORM == kFormC ? f32pair_from_bits(bits) : bits;
+}
+
+// Tile-staged TMA path, as the xorshift fill kernel: warp g owns streams 32g .. 32g+31, 16
+// outputs per lane per chunk through a 128-byte-swizzled tile and one 2D tensor store.
+template <int FORM>
+__global__ void __launch_bounds__(256) fill_mrg_tma_kernel(const FillParams p, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t base = (smem_addr(smem_raw) + 1023u) & ~1023u;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const uint64_t warp_global = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+  if (warp_global * 32 >= p.n_streams) return;
+  const uint64_t stream = warp_global * 32 + lane;
+  const bool active = stream < p.n_streams;
+  Mrg32k3a g = active ? mrg_load(p.state, stream) : Mrg32k3a{1u, 2u, 3u, 4u, 5u, 6u};
+  uint32_t rej = 0;
+  const uint32_t tile = base + (uint32_t)warp * kTileBytes;
+  const uint32_t row_off = (uint32_t)lane * 128u;
+  const uint32_t sw = (uint32_t)(lane & 7);
+  const int y0 = (int)(warp_global * 32);
+  for (uint64_t x0 = 0; x0 < p.per_stream; x0 += kChunk) {
+    uint64_t v[kChunk];
+    const uint64_t left = p.per_stream - x0;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) v[j] = ((uint64_t)j < left) ? mrg_next_output<FORM>(g, rej, p) : 0ull;
+    if (lane == 0) bulk_wait_read<0>();
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < kChunk / 2; ++c)
+      st_shared_v2(tile + row_off + (((uint32_t)c ^ sw) << 4), v[2 * c], v[2 * c + 1]);
+    fence_async_shared();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_2d(&tmap, tile, (int)x0, y0);
+      bulk_commit();
+    }
+  }
+  if (lane == 0) bulk_wait_all();
+  if (active) {
+    mrg_store(p.state, stream, g);
+    if (p.rejects) p.rejects[stream] = rej;
+  }
+}
+
+// Plain stores (any alignment, host-mapped outputs): each thread writes its own stream.
+template <int FORM>
+__global__ void __launch_bounds__(256) fill_mrg_plain_kernel(const FillParams p) {
+  const uint64_t stream = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (stream >= p.n_streams) return;
+  Mrg32k3a g = mrg_load(p.state, stream);
+  uint32_t rej = 0;
+  uint64_t* dst = p.out + stream * p.per_stream;
+  for (uint64_t i = 0; i < p.per_stream; ++i) dst[i] = mrg_next_output<FORM>(g, rej, p);
+  mrg_store(p.state, stream, g);
+  if (p.rejects) p.rejects[stream] = rej;
+}
+
+}  // namespace prngd
+
+namespace prngd_host {
+
+// Division constants of D = (m1 - 1)^2 (normalised by its own shift) and RN(1/D).
+static prngd::DivConst mrg_divconst() {
+  const uint64_t m = prngd::kMrgM1 - 1u;
+  const uint64_t d = m * m;
+  prngd::DivConst dc;
+  dc.sh = prngd::clz64(d);
+  dc.d_norm = d << dc.sh;
+  const unsigned __int128 all = ~(unsigned __int128)0;
+  dc.v = (uint64_t)(all / dc.d_norm - ((unsigned __int128)1 << 64));
+  return dc;
+}
+
+namespace {
+constexpr int kWarpsPerBlock = 8;
+constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * prngd::kTileBytes + 1024;
+
+template <int FORM>
+cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((p.n_streams + 255) / 256);
+  if (map) {
+    auto k = prngd::fill_mrg_tma_kernel<FORM>;
+    static bool attr = false;
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
+  } else {
+    prngd::fill_mrg_plain_kernel<FORM><<<blocks, 256, 0, s>>>(p);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
+                    uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode) {
+  if (n_streams == 0 || per_stream == 0) return PRNG_OK;
+  if (mode != 0 || (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR))
+    return fail(PRNG_EINVAL, "MRG32k3a streams take forms A, B and C with mode 0");
+  if (allow_tma && device_mapped_host(out, nullptr)) allow_tma = false;
+  prngd::FillParams p;
+  memset(&p, 0, sizeof(p));
+  p.state = state;
+  p.n_streams = n_streams;
+  p.per_stream = per_stream;
+  p.out = (uint64_t*)out;
+  p.rejects = rejects;
+  p.dc = h->dc;
+  p.scale = h->scale;
+  p.w = 32;
+  p.one = 1;
+  CUtensorMap map;
+  const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
+  cudaError_t e;
+  switch (form) {
+    case PRNG_FORM_A_FP64: e = launch_mrg_form<prngd::kFormA>(p, mp, s); break;
+    case PRNG_FORM_C_F32PAIR: e = launch_mrg_form<prngd::kFormC>(p, mp, s); break;
+    default: e = launch_mrg_form<prngd::kFormB>(p, mp, s); break;
+  }
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "MRG32k3a fill launch: %s", cudaGetErrorString(e));
+  return PRNG_OK;
+}
+
+}  // namespace prngd_host
+
+using namespace prngd_host;
+
+extern "C" {
+
+int prng_create_mrg32k3a(prng_t* out, uint64_t seed, uint64_t n_streams) {
+  if (!out) return fail(PRNG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n_streams == 0 || n_streams > (1ull << 32)) return fail(PRNG_EINVAL, "n_streams must be in [1, 2^32]");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(PRNG_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  prng_ctx* h = new prng_ctx();
+  h->device = dev;
+  h->seed = seed;
+  h->n_streams = n_streams;
+  h->w = 32;
+  h->gen = PRNG_GEN_MRG32K3A;
+  h->dc = mrg_divconst();
+  const uint64_t one = prngd::rn_bits_exact(1, h->dc);  // RN(1/D)
+  memcpy(&h->scale, &one, 8);
+  e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_state, n_streams * 2 * sizeof(uint4));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(PRNG_ENOMEM, "MRG32k3a state (%llu bytes): %s", (unsigned long long)(n_streams * 32),
+                cudaGetErrorString(e));
+  }
+  prngd::mrg_seed_kernel<<<(unsigned)((n_streams + 255) / 256), 256>>>(h->d_state, n_streams, seed);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+  if (e != cudaSuccess) {
+    cudaFree(h->d_state);
+    delete h;
+    return fail(PRNG_ECUDA, "MRG32k3a seeding: %s", cudaGetErrorString(e));
+  }
+  *out = h;
+  return PRNG_OK;
+}
+
+int prng_generator(prng_t h) { return h ? h->gen : -1; }
+
+}  // extern "C"

@@ -75,7 +75,7 @@ extern "C" int prng_fill_f64_host_noalloc(prng_t h, double* host_out, uint64_t p
   // kernel writes every value and every reject count of the slice.
   for (uint64_t s0 = 0; s0 < h->n_streams; s0 += slice) {
     const uint64_t cnt = (h->n_streams - s0 < slice) ? h->n_streams - s0 : slice;
-    rc = prngd_host::launch_fill(h, h->d_state + s0, cnt, d_values, per_stream, form,
+    rc = prngd_host::launch_fill(h, prngd_host::state_at(h, s0), cnt, d_values, per_stream, form,
                                  host_rejects ? d_rej : nullptr, s, true);
     if (rc) return rc;
     e = cudaMemcpyAsync(host_out + s0 * per_stream, d_values, (size_t)cnt * per_stream * 8, cudaMemcpyDeviceToHost, s);

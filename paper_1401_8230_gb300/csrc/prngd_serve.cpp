@@ -207,6 +207,8 @@ int prng_server_create(prng_server_t* out, prng_t h, uint64_t streams_per_client
                        size_t pool_bytes) {
   if (!out || !h) return fail(PRNG_EINVAL, "null argument");
   *out = nullptr;
+  if (prng_generator(h) != PRNG_GEN_XORSHIFT128)
+    return fail(PRNG_EINVAL, "the serving loop runs on xorshift128 streams only");
   uint64_t n_streams = 0;
   int w = 0;
   int rc = prng_get_info(h, &n_streams, &w);
