@@ -529,10 +529,24 @@ def e2e(torch, P, g, samples_step):
     g.fill_f64_host(pageable, PER_STREAM, P.FORM_B_INTBITS)
     dt_pageable = time.perf_counter() - t0
     del pageable
+    # the host link itself: a plain device-to-pinned-host copy of the same bytes (copy engine)
+    dev = torch.empty(samples_step, dtype=torch.float64, device="cuda")
+    pinned = torch.empty(samples_step, dtype=torch.float64, pin_memory=True)
+    pinned.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        pinned.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    dt_copy = (time.perf_counter() - t0) / reps
+    del dev, pinned
+    link_gbs = samples_step * 8 / dt_copy / 1e9
     return {"value": samples_step / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": samples_step * 8, "ms_per_step": dt * 1e3,
             "api": "prng_fill_f64_host (pinned host buffer: direct device writes)",
-            "pageable_gsamples_s": samples_step / dt_pageable / 1e9}
+            "pageable_gsamples_s": samples_step / dt_pageable / 1e9,
+            "host_link_copy_gbs": link_gbs,
+            "host_link_frac": samples_step * 8 / dt / 1e9 / link_gbs}
 
 
 if __name__ == "__main__":

@@ -101,9 +101,9 @@ __device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, cons
   } else if constexpr (FORM == kFormA) {
     double z;
     if constexpr ((MAP & kMapEq5) != 0) {
-      z = __dmul_rn(__ull2double_rn(((uint64_t)(u1 - 1u) << w) + u2), p.scale5);  // RN(RN(m) C5)
+      z = __dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(((uint64_t)(u1 - 1u) << w) + u2)), p.scale5);  // RN(RN(m) C5)
     } else {
-      z = __dmul_rn(__ull2double_rn(numerator(u1, u2, w)), p.scale);  // RN(RN(n) C_w)
+      z = __dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(numerator(u1, u2, w))), p.scale);  // RN(RN(n) C_w)
     }
     if constexpr ((MAP & kMapOneMinus) != 0) z = __dsub_rn(1.0, z);
     return (uint64_t)__double_as_longlong(z);

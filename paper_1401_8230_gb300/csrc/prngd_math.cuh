@@ -180,6 +180,20 @@ PRNGD_HD uint64_t numerator(uint32_t u1, uint32_t u2, int w) {
   return ((uint64_t)(u1 - 1u) << w) + (uint64_t)u2 + 1u;
 }
 
+// Double bits of n (n >= 1) rounded to nearest even, by integer operations: the FP64 unit's
+// unsigned-to-double conversion runs at about half the rate of its multiply on this GPU.
+// L = bit length of n; up to 53 bits the value is exact, above that n is cut at bit s = L - 53
+// and rounded up when the cut part is more than half, or exactly half with an odd result.
+// A mantissa that rounds up to 2^53 carries into the exponent.
+PRNGD_HD uint64_t u64_to_f64_bits(uint64_t n) {
+  const int L = 64 - clz64(n);
+  if (L <= 53) return ((uint64_t)(L + 1021) << 52) + (n << (53 - L));
+  const int s = L - 53;
+  const uint64_t q = n >> s, rem = n & ((1ull << s) - 1), half = 1ull << (s - 1);
+  const uint64_t up = (rem > half || (rem == half && (q & 1))) ? 1u : 0u;
+  return ((uint64_t)(L + 1021) << 52) + q + up;
+}
+
 // ------------------------------------------------------------------------ exact division
 // Constants for dividing by D without a hardware divide: D' = D << sh is D normalised to a
 // set top bit, and v = floor((2^128 - 1) / D') - 2^64 is its Moller-Granlund reciprocal

@@ -58,7 +58,7 @@ __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, 
     ++rej;
   }
   const uint64_t n = (uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u);
-  if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
+  if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(n)), p.scale));
   const uint64_t bits = rn_bits_exact(n, p.dc);
   return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }

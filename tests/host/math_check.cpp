@@ -155,6 +155,30 @@ int main(int argc, char** argv) {
       const uint64_t want = ((uint64_t)(bl - 1 - 96 + 1022) << 52) + m;
       expect(rn_bits_from_scaled96(t2, t1, t0), want, "scaled96", t2, t1);
     }
+  // 4b. unsigned 64-bit to double, round to nearest even, against the host's IEEE conversion:
+  //     exact ties at every cut position, values around powers of two, random values
+  {
+    auto check = [&](uint64_t n) {
+      const double d = (double)n;
+      expect(u64_to_f64_bits(n), bits_of(d), "u64_to_f64", (uint32_t)(n >> 32), (uint32_t)n);
+    };
+    for (int s = 1; s <= 11; ++s)
+      for (int k = 0; k < 2000; ++k) {
+        const uint64_t q = (1ull << 52) | (rng() & ((1ull << 52) - 1));  // 53-bit head
+        if ((q << s) >> s != q) continue;
+        const uint64_t base = q << s, half = 1ull << (s - 1);
+        const uint64_t ds[5] = {half - 1, half, half + 1, 0, (1ull << s) - 1};
+        for (uint64_t d : ds) check(base + d);
+      }
+    for (int L = 1; L <= 64; ++L)
+      for (int64_t d = -3; d <= 3; ++d) {
+        const uint64_t p2 = (L == 64) ? 0 : (1ull << L);
+        const uint64_t n = p2 + (uint64_t)d;
+        if (n) check(n);
+      }
+    check(~0ull);
+    for (int i = 0; i < 200000; ++i) check((rng() >> (rng() % 64)) | 1u);
+  }
   // 5. Eq. 5 and 1 - z: constants, the exact 128-bit path and the fast paths against the oracle
   {
     const DivConst a = make_dc_eq5(32), b = divconst_eq5_for<32>(), c = make_dc_eq5(24), d = divconst_eq5_for<24>();
