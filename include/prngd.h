@@ -181,6 +181,19 @@ int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mo
                     uint64_t* d_rejects, void* cuda_stream);
 
 /*
+ * prng_convert_pairs -- the method's conversion (Section 2: Eq. 4, or Eq. 5 / 1 - z by `mode`)
+ * applied to given w-bit base draws, with the same device code as the fills: output i is the
+ * form-`form` value (A, B, C or L) of the pair (d_u1[i], d_u2[i]) (values taken modulo 2^w).
+ * A pair whose u1 is rejected (0 or 2^w - 1) gives all-ones bits (a NaN); the reject rule bit of
+ * `mode` is ignored (there is no stream to redraw from). For callers with their own base draws,
+ * and for testing the conversions on chosen inputs. No handle; asynchronous on cuda_stream.
+ * d_u1, d_u2: device arrays of n uint32; d_out: device array of n 8-byte outputs.
+ * Errors: PRNG_EINVAL (w outside [2, 32], unknown form or mode bits, null pointers), PRNG_ECUDA.
+ */
+int prng_convert_pairs(int w, int form, int mode, const uint32_t* d_u1, const uint32_t* d_u2, uint64_t n,
+                       uint64_t* d_out, void* cuda_stream);
+
+/*
  * prng_fill_f64_host -- end-to-end fill into HOST memory: the same values as prng_fill_f64
  * (the streams advance identically) into `host_out` (n_streams * per_stream doubles). If
  * host_out is pinned (page-locked and mapped for the device), one kernel writes it directly

@@ -56,6 +56,7 @@ _SIGNATURES = {
     "prng_fill_mode": (_i32, [_P, _vp, _u64, ctypes.c_int, ctypes.c_int, _vp, _vp]),
     "prng_fill_split": (_i32, [_P, _vp, _u64, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, _vp, _vp]),
     "prng_skip": (_i32, [_P, _u64, _vp]),
+    "prng_convert_pairs": (_i32, [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _u64, _vp, _vp]),
     "prng_fill_f64_host": (_i32, [_P, _vp, _u64, _i32, _vp]),
     "prng_fill_f64_host_noalloc": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
@@ -191,6 +192,10 @@ def prng_fill_mode(h: int, out, per_stream: int, form: int, mode: int, rejects=N
 def prng_fill_split(h: int, out, per_stream: int, form: int, mode: int = 0, segments: int = 0, rejects=None,
                     stream=None) -> None:
     _check(lib().prng_fill_split(h, _ptr(out), per_stream, form, mode, segments, _ptr(rejects), _stream(stream)))
+
+
+def prng_convert_pairs(w: int, form: int, mode: int, u1, u2, n: int, out, stream=None) -> None:
+    _check(lib().prng_convert_pairs(w, form, mode, _ptr(u1), _ptr(u2), n, _ptr(out), _stream(stream)))
 
 
 def prng_skip(h: int, draws: int, stream=None) -> None:

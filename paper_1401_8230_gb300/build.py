@@ -22,7 +22,7 @@ OBJ_DIR = os.path.join(HERE, "_build")
 
 SOURCES = ["prngd.cu", "prngd_io.cu", "prngd_stats.cu", "prngd_noalloc.cu", "prngd_batch.cu", "prngd_serve.cpp",
            "prngd_modes.cu", "prngd_modes_fast.cu", "prngd_jump.cu",
-           "prngd_mrg.cu"]
+           "prngd_mrg.cu", "prngd_convert.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

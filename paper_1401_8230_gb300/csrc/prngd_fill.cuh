@@ -101,7 +101,8 @@ __device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, cons
   } else if constexpr (FORM == kFormA) {
     double z;
     if constexpr ((MAP & kMapEq5) != 0) {
-      z = __dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(((uint64_t)(u1 - 1u) << w) + u2)), p.scale5);  // RN(RN(m) C5)
+      const uint64_t m = ((uint64_t)(u1 - 1u) << w) + u2;  // 0 for the pair mapped to z' = 0
+      z = __dmul_rn(__longlong_as_double((long long)(m ? u64_to_f64_bits(m) : 0ull)), p.scale5);  // RN(RN(m) C5)
     } else {
       z = __dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(numerator(u1, u2, w))), p.scale);  // RN(RN(n) C_w)
     }
@@ -121,31 +122,6 @@ __device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, cons
       bits = rn_bits_exact(numerator(a1, a2, w), p.dc);
     }
     return FORM == kFormC ? f32pair_from_bits(bits) : bits;
-  }
-}
-
-// The output of an accepted pair by the fastest valid path: at w = 32, forms B and C, the fast
-// path, then the medium path for small values, else the exact conversion.
-template <int W, int FORM, int MAP>
-__device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, const FillParams& p) {
-  if constexpr (W == 32 && (FORM == kFormB || FORM == kFormC)) {
-    constexpr bool kComp = (MAP & kMapOneMinus) != 0;
-    const uint32_t a1 = kComp ? ~u1 : u1, a2 = kComp ? ~u2 : u2;
-    uint64_t bits;
-    if constexpr ((MAP & kMapEq5) != 0) {
-      const uint64_t Y = fast32_eq5_Y(a1, a2);
-      if (fast32_eq5_ok(a1, Y)) bits = fast32_eq5_bits(a1, a2, Y, kComp ? 1u : 0u);
-      else if (medium32_eq5_ok(a1, a2)) bits = medium32_eq5_bits(a1, a2, Y, kComp ? 1u : 0u);
-      else return convert_exact<W, FORM, MAP>(u1, u2, p);
-    } else {
-      const uint64_t X = fast32_X(a1, a2);
-      if (fast32_ok(a1, X)) bits = fast32_bits(a1, a2, X);
-      else if (medium32_ok(a1, X, a2)) bits = medium32_bits(a1, a2, X);
-      else return convert_exact<W, FORM, MAP>(u1, u2, p);
-    }
-    return FORM == kFormC ? f32pair_from_bits(bits) : bits;
-  } else {
-    return convert_exact<W, FORM, MAP>(u1, u2, p);
   }
 }
 
@@ -260,6 +236,53 @@ __device__ __forceinline__ uint64_t fast32_bits_ptx(uint32_t u1, uint32_t u2, ui
   return fast32_bits_ptx_t<3, -1, 1, 0xFFFFFFF8u>(u1, u2, one, ok);
 }
 
+// The w = 24 fast path of fast24_ok / fast24_bits as PTX, from the raw 32-bit words (the draws
+// are their top 24 bits). With c1 = 3 u1 + 2 u2 - 1 (= 2B + 3A) and c2 = 4 u1 + 3 u2 - 1
+// (= 3B + 4A), K = c1 2^24 + c2, L = (2 u1 + u2 - 1) 2^16 + (K >> 32) and
+// I = (u1 - 1) 2^40 + L; then the same rounding as at w = 32. Returns 1 in `ok` when
+// 2^14 <= A <= 2^24 - 3 and the low word of K is below 2^32 - 16.
+__device__ __forceinline__ uint64_t fast24_bits_ptx(uint32_t x, uint32_t y, uint32_t one, uint32_t& ok) {
+  uint32_t lo, hi;
+  asm("{\n\t"
+      ".reg .u64 K, C2, KH, L;\n\t"
+      ".reg .u32 u1, u2, t, c1, t2, c2, klo, khi, a, d, llo, lhi, a8, ihi, q, s, rb, jlo, jhi, s1, mhi, e;\n\t"
+      ".reg .pred p1, p2;\n\t"
+      "shr.u32 u1, %3, 8;\n\t"
+      "shr.u32 u2, %4, 8;\n\t"
+      "mad.lo.u32 t, u2, 2, -1;\n\t"
+      "mad.lo.u32 c1, u1, 3, t;\n\t"            // 3 u1 + 2 u2 - 1
+      "mad.lo.u32 t2, u2, 3, -1;\n\t"
+      "mad.lo.u32 c2, u1, 4, t2;\n\t"           // 4 u1 + 3 u2 - 1
+      "cvt.u64.u32 C2, c2;\n\t"
+      "mad.wide.u32 K, c1, 16777216, C2;\n\t"   // K = c1 2^24 + c2
+      "mov.b64 {klo, khi}, K;\n\t"
+      "mad.lo.u32 a, u1, %5, -16385;\n\t"       // u1 - (2^14 + 1)
+      "setp.lt.u32 p1, a, 0xFFBFFE;\n\t"        // 2^14 <= A <= 2^24 - 3
+      "setp.lt.and.u32 p2, klo, 0xFFFFFFF0, p1;\n\t"
+      "selp.u32 %1, 1, 0, p2;\n\t"
+      "mad.lo.u32 d, u1, 2, u2;\n\t"
+      "mad.lo.u32 d, d, %5, -1;\n\t"            // 2 u1 + u2 - 1
+      "cvt.u64.u32 KH, khi;\n\t"
+      "mad.wide.u32 L, d, 65536, KH;\n\t"       // L = d 2^16 + (K >> 32)
+      "mov.b64 {llo, lhi}, L;\n\t"
+      "mad.lo.u32 a8, u1, 256, -256;\n\t"       // A 2^8
+      "mad.lo.u32 ihi, lhi, %5, a8;\n\t"        // I high word (I low word = llo)
+      "bfind.u32 q, ihi;\n\t"
+      "mad.lo.u32 s, q, %5, -21;\n\t"
+      "shl.b32 rb, 1, s;\n\t"
+      "add.cc.u32 jlo, llo, rb;\n\t"            // J = I + 2^s
+      "addc.u32 jhi, ihi, 0;\n\t"
+      "mad.lo.u32 s1, q, %5, -20;\n\t"
+      "shf.r.wrap.b32 %2, jlo, jhi, s1;\n\t"
+      "shr.u32 mhi, jhi, s1;\n\t"
+      "mad.lo.u32 e, q, 0x100000, 0x3DE00000;\n\t"
+      "mad.lo.u32 %0, mhi, %5, e;\n\t"
+      "}"
+      : "=r"(hi), "=r"(ok), "=r"(lo)
+      : "r"(x), "r"(y), "r"(one));
+  return ((uint64_t)hi << 32) | lo;
+}
+
 struct PairOut {
   uint64_t v0, v1;
   uint32_t x, y, z, w, rej;
@@ -286,6 +309,50 @@ __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, ui
     v[k] = exact_bc<W, FORM, MAP>(u1, u2);
   }
   return PairOut{v[0], v[1], st.x, st.y, st.z, st.w, rej};
+}
+
+// The output of an accepted pair by the fastest valid path, with the pair path's own code: at
+// w = 32 and w = 24 (forms B and C) the fast path (PTX where the pair path uses PTX), then the
+// medium path for small values, else the exact conversion.
+template <int W, int FORM, int MAP>
+__device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, const FillParams& p) {
+  if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
+    constexpr bool kComp = (MAP & kMapOneMinus) != 0;
+    constexpr uint32_t top = (W == 32) ? 0xFFFFFFFFu : 0xFFFFFFu;
+    const uint32_t a1 = kComp ? top - u1 : u1, a2 = kComp ? top - u2 : u2;
+    uint64_t bits;
+    if constexpr (W == 32 && (MAP & kMapEq5) != 0) {
+      uint32_t ok;
+      bits = fast32_bits_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(a1, a2, p.one, ok);
+      if (!ok) {
+        if (medium32_eq5_ok(a1, a2)) bits = medium32_eq5_bits(a1, a2, fast32_eq5_Y(a1, a2), kComp ? 1u : 0u);
+        else return convert_exact<W, FORM, MAP>(u1, u2, p);
+      }
+    } else if constexpr (W == 32) {
+      uint32_t ok;
+      bits = fast32_bits_ptx(a1, a2, p.one, ok);
+      if (!ok) {
+        const uint64_t X = fast32_X(a1, a2);
+        if (medium32_ok(a1, X, a2)) bits = medium32_bits(a1, a2, X);
+        else return convert_exact<W, FORM, MAP>(u1, u2, p);
+      }
+    } else if constexpr ((MAP & kMapEq5) != 0) {
+      const uint64_t K = fast24_eq5_K(a1, a2);
+      if (!fast24_eq5_ok(a1, K)) return convert_exact<W, FORM, MAP>(u1, u2, p);
+      bits = fast24_eq5_bits(a1, a2, K, kComp ? 0x10000u : 0u);
+    } else {
+      uint32_t ok;
+      bits = fast24_bits_ptx(a1 << 8, a2 << 8, p.one, ok);  // raw words: the draws in their top 24 bits
+      if (!ok) {
+        const uint64_t K = fast24_K(a1, a2);
+        if (medium24_ok(a1, K, a2)) bits = medium24_bits(a1, a2, K);
+        else return convert_exact<W, FORM, MAP>(u1, u2, p);
+      }
+    }
+    return FORM == kFormC ? f32pair_from_bits(bits) : bits;  // the fast and medium values are not 0
+  } else {
+    return convert_exact<W, FORM, MAP>(u1, u2, p);
+  }
 }
 
 // Two outputs of a w = 32 or w = 24 stream (forms B and C) from one 4-draw block, with one
@@ -347,11 +414,10 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
     v1 = fast32_bits_ptx(dz, dw, p.one, ok1);
     ok = ok0 & ok1;
   } else {
-    const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
-    const uint64_t Ka = fast24_K(u1a, u2a), Kb = fast24_K(u1b, u2b);
-    ok = fast24_ok(u1a, Ka) & fast24_ok(u1b, Kb);
-    v0 = fast24_bits(u1a, u2a, Ka);
-    v1 = fast24_bits(u1b, u2b, Kb);
+    uint32_t ok0, ok1;
+    v0 = fast24_bits_ptx(dx, dy, p.one, ok0);
+    v1 = fast24_bits_ptx(dz, dw, p.one, ok1);
+    ok = ok0 & ok1;
   }
   if (__builtin_expect(ok == 0, 0)) {
     // Almost always a small value (A < 2^22 at w = 32): the inline medium path. Rejects and

@@ -68,6 +68,9 @@ inline uint4* state_at(prng_ctx* h, uint64_t s) { return h->d_state + (h->gen ==
 // PRNG_EINVAL unless the handle's streams are xorshift128 (paths built on its GF(2) structure,
 // its fast conversions or its 16-byte state).
 int require_xorshift(prng_ctx* h, const char* what);
+// Division constants of D = (2^w - 1)^2 and the form-A scale RN(1/D).
+prngd::DivConst make_divconst(int w);
+double scale_constant(const prngd::DivConst& dc);
 // Mode-dependent constants of FillParams (reject rule, Eq. 5 division constants, form L).
 void set_mode_constants(prngd::FillParams& p, int w, int mode);
 void release_batch(prng_ctx* h);

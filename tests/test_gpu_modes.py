@@ -77,7 +77,7 @@ def test_plain_store_path(form):
 def test_reject_rules_at_small_w(w, mode):
     """Rejects are frequent at small w (2/2^w of attempts), so both rules are exercised."""
     seed, ns, per = 77, 64, 258
-    for form in (P.FORM_B_INTBITS, P.FORM_L_ALGO1):
+    for form in (P.FORM_B_INTBITS, P.FORM_L_ALGO1, P.FORM_A_FP64):
         with P.Generator(seed, ns, w) as g:
             got, rej = run(g, per, form, mode)
             want, wrej = O.fill(seed, 0, ns, per, w, OF[form], omode(mode))
