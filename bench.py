@@ -24,6 +24,7 @@ import os
 import re
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 from concurrent.futures import ThreadPoolExecutor
@@ -107,7 +108,9 @@ class ClockSampler:
 
     def __init__(self, device_index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device_index}.csv")
+        # raw samples beside the run (only their summary goes into the JSON line)
+        self.path = os.path.join(os.environ.get("PRNGD_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"prngd_clocks_rank{device_index}.csv")
         self.dev = device_index
 
     def start(self):
