@@ -325,8 +325,9 @@ def main():
     g.close()
     if rank == 0 and not args.no_batched:
         torch.cuda.empty_cache()
+        eq5_rate = line.get("forms", {}).get("w32_eq5_formB", {}).get("gsamples_s")
         line["batched"] = batched(torch, P, stream, plain_rate, args.batched_requests, args.batched_hi,
-                                  not args.no_autotune)
+                                  not args.no_autotune, eq5_rate)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_served:
         mix_rate = None
@@ -412,12 +413,13 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
 TUNE_TABLE = os.path.join(ROOT, "paper_1401_8230_gb300", "lib", "autotune.txt")
 
 
-def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True):
+def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, eq5_rate=None):
     """4096 fresh requests, log-uniform lengths in [2^8, 2^26], own seeds and stream offsets,
     w = 32 form B, one persistent launch (graph replay) with the autotuned shape; against the
     same requests as 4096 single-request launches. Each request's output starts on a 256-byte
     boundary of one pool (as separately allocated outputs would); the same batch packed at
-    16-byte offsets is timed too."""
+    16-byte offsets is timed too, and the same batch with every request under the Eq. 5 map
+    (the any-mode kernel)."""
     from paper_1401_8230_gb300 import workloads
 
     spec = workloads.batched_requests(n=n_req, lo=2**8, hi=hi, seed=1)
@@ -425,13 +427,14 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True):
     g = P.Generator(SEED, 1, W)
     tuned = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, hi, TUNE_TABLE) if tune else None
 
-    def place(align):
+    def place(align, mode=0):
         """One pool, request i at a multiple of `align` outputs; returns (pool, request array)."""
         sizes = [((r["length"] + 1) // 2 * 2 + align - 1) // align * align for r in spec]
         pool = torch.empty(sum(sizes) + 32, dtype=torch.float64, device="cuda")
         reqs, off = [], 0
         for r, sz in zip(spec, sizes):
-            reqs.append(P.fresh_request(pool[off:], r["length"], r["seed"], r["first_stream"], P.FORM_B_INTBITS))
+            reqs.append(P.fresh_request(pool[off:], r["length"], r["seed"], r["first_stream"], P.FORM_B_INTBITS,
+                                        0, None, mode))
             off += sz
         return pool, reqs, (P.Request * len(reqs))(*reqs)
 
@@ -441,6 +444,10 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True):
 
     pool, reqs, arr = place(2)  # 16-byte packing
     packed_ms = batch_ms(arr)
+    del pool, reqs, arr
+    torch.cuda.empty_cache()
+    pool, reqs, arr = place(32, P.MODE_EQ5)  # the Eq. 5 map: any-mode kernel
+    eq5_ms = batch_ms(arr)
     del pool, reqs, arr
     torch.cuda.empty_cache()
     pool, reqs, arr = place(32)  # 256-byte aligned
@@ -466,9 +473,12 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True):
     g.close()
     rate = total / (ms * 1e-3) / 1e9
     packed = total / (packed_ms * 1e-3) / 1e9
+    eq5 = total / (eq5_ms * 1e-3) / 1e9
     return {"requests": len(spec), "outputs": total, "placement": "256-byte aligned outputs in one pool",
             "gsamples_s": rate, "ms": ms, "vs_plain_fill": rate / plain_rate,
             "packed_16B": {"gsamples_s": packed, "ms": packed_ms, "vs_plain_fill": packed / plain_rate},
+            "eq5_map": {"gsamples_s": eq5, "ms": eq5_ms, "kernel": "any-mode",
+                        "vs_plain_eq5_fill": (eq5 / eq5_rate) if eq5_rate else None},
             "per_request_launches_gsamples_s": total / (plain_ms * 1e-3) / 1e9,
             "per_request_launches_ms": plain_ms, "shape": tuned, "graph": True}
 

@@ -277,13 +277,14 @@ int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist, uint64_t* 
 
 typedef struct prng_request {
   int32_t kind;          /* PRNG_REQ_FRESH or PRNG_REQ_RESIDENT */
-  int32_t form;          /* PRNG_FORM_A_FP64, PRNG_FORM_B_INTBITS or PRNG_FORM_C_F32PAIR */
+  int32_t form;          /* PRNG_FORM_A_FP64, PRNG_FORM_B_INTBITS, PRNG_FORM_C_F32PAIR or
+                            PRNG_FORM_L_ALGO1 */
   uint64_t length;       /* outputs, >= 1 */
   uint64_t seed;         /* FRESH: seed of the request's streams */
   uint64_t first_stream; /* FRESH: first stream id; RESIDENT: first stream of the handle */
   uint64_t n_streams;    /* RESIDENT: streams of the handle to continue (FRESH: ignored) */
   uint32_t chunk;        /* FRESH: outputs per stream, even (0 = 1024); RESIDENT: ignored */
-  uint32_t reserved;     /* 0 */
+  uint32_t mode;         /* PRNG_MODE_* bits as for prng_fill_mode (0: Eq. 4, pair rejects) */
   void* d_out;           /* device pointer, 16-byte aligned */
   uint64_t* d_rejects;   /* nullable device pointer, one count per row */
 } prng_request;
@@ -358,6 +359,9 @@ int prng_server_create(prng_server_t* out, prng_t h, uint64_t streams_per_client
                        uint64_t min_per_stream, size_t pool_bytes);
 int prng_server_destroy(prng_server_t s);
 int prng_server_submit(prng_server_t s, uint64_t client, uint64_t length, int form, uint64_t* id);
+/* As prng_server_submit, with the request's PRNG_MODE_* bits (prng_server_submit: mode 0). */
+int prng_server_submit_mode(prng_server_t s, uint64_t client, uint64_t length, int form, uint32_t mode,
+                            uint64_t* id);
 int prng_server_step(prng_server_t s);
 int prng_server_poll(prng_server_t s, uint64_t id, int* done, void** d_out);
 int prng_server_read(prng_server_t s, uint64_t id, void* host_dst, size_t bytes);
@@ -379,7 +383,7 @@ typedef struct prng_trace_item {
   uint64_t client;
   uint64_t length;  /* outputs */
   int32_t form;
-  int32_t reserved;
+  uint32_t mode;    /* PRNG_MODE_* bits */
 } prng_trace_item;
 int prng_server_run_trace(prng_server_t s, const prng_trace_item* items, uint64_t n, double* latency,
                           double* makespan, double timeout_s);

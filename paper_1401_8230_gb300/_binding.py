@@ -18,23 +18,26 @@ MAX_BATCH_REQUESTS = 4096
 class TraceItem(ctypes.Structure):
     """struct prng_trace_item of include/prngd.h."""
     _fields_ = [("t", ctypes.c_double), ("client", ctypes.c_uint64), ("length", ctypes.c_uint64),
-                ("form", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("form", ctypes.c_int32), ("mode", ctypes.c_uint32)]
 
 
 class Request(ctypes.Structure):
     """struct prng_request of include/prngd.h."""
     _fields_ = [("kind", ctypes.c_int32), ("form", ctypes.c_int32), ("length", ctypes.c_uint64),
                 ("seed", ctypes.c_uint64), ("first_stream", ctypes.c_uint64), ("n_streams", ctypes.c_uint64),
-                ("chunk", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("d_out", ctypes.c_void_p),
+                ("chunk", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("d_out", ctypes.c_void_p),
                 ("d_rejects", ctypes.c_void_p)]
 
 
-def fresh_request(out, length: int, seed: int, first_stream: int, form: int = 1, chunk: int = 0, rejects=None):
-    return Request(REQ_FRESH, form, length, seed & (2**64 - 1), first_stream, 0, chunk, 0, _ptr(out), _ptr(rejects))
+def fresh_request(out, length: int, seed: int, first_stream: int, form: int = 1, chunk: int = 0, rejects=None,
+                  mode: int = 0):
+    return Request(REQ_FRESH, form, length, seed & (2**64 - 1), first_stream, 0, chunk, mode, _ptr(out),
+                   _ptr(rejects))
 
 
-def resident_request(out, length: int, first_stream: int, n_streams: int, form: int = 1, rejects=None):
-    return Request(REQ_RESIDENT, form, length, 0, first_stream, n_streams, 0, 0, _ptr(out), _ptr(rejects))
+def resident_request(out, length: int, first_stream: int, n_streams: int, form: int = 1, rejects=None,
+                     mode: int = 0):
+    return Request(REQ_RESIDENT, form, length, 0, first_stream, n_streams, 0, mode, _ptr(out), _ptr(rejects))
 
 _lock = threading.Lock()
 _lib: ctypes.CDLL | None = None
@@ -71,6 +74,7 @@ _SIGNATURES = {
     "prng_server_create": (_i32, [ctypes.POINTER(_P), _P, _u64, _u64, _sz]),
     "prng_server_destroy": (_i32, [_P]),
     "prng_server_submit": (_i32, [_P, _u64, _u64, _i32, ctypes.POINTER(_u64)]),
+    "prng_server_submit_mode": (_i32, [_P, _u64, _u64, _i32, ctypes.c_uint32, ctypes.POINTER(_u64)]),
     "prng_server_step": (_i32, [_P]),
     "prng_server_poll": (_i32, [_P, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_vp)]),
     "prng_server_read": (_i32, [_P, _u64, _vp, _sz]),
@@ -269,6 +273,12 @@ def prng_server_submit(s: int, client: int, length: int, form: int = FORM_B_INTB
     return int(i.value)
 
 
+def prng_server_submit_mode(s: int, client: int, length: int, form: int, mode: int) -> int:
+    i = _u64()
+    _check(lib().prng_server_submit_mode(s, client, length, form, mode, ctypes.byref(i)))
+    return int(i.value)
+
+
 def prng_server_step(s: int) -> None:
     _check(lib().prng_server_step(s))
 
@@ -299,10 +309,12 @@ def prng_server_info(s: int) -> dict:
 
 
 def prng_server_run_trace(s: int, items, timeout_s: float = 600.0):
-    """Replay [(t, client, length, form), ...] in real time; returns (latencies, makespan)."""
+    """Replay [(t, client, length, form), ...] or [(t, client, length, form, mode), ...] in real
+    time; returns (latencies, makespan)."""
     import numpy as np
 
-    arr = (TraceItem * len(items))(*[TraceItem(float(t), int(c), int(L), int(f), 0) for t, c, L, f in items])
+    arr = (TraceItem * len(items))(*[TraceItem(float(it[0]), int(it[1]), int(it[2]), int(it[3]),
+                                               int(it[4]) if len(it) > 4 else 0) for it in items])
     lat = np.zeros(len(items), dtype=np.float64)
     mk = _dbl()
     _check(lib().prng_server_run_trace(s, ctypes.addressof(arr), len(items), lat.ctypes.data, ctypes.byref(mk),

@@ -23,6 +23,8 @@ OBJ_DIR = os.path.join(HERE, "_build")
 SOURCES = ["prngd.cu", "prngd_io.cu", "prngd_stats.cu", "prngd_noalloc.cu", "prngd_batch.cu", "prngd_serve.cpp",
            "prngd_modes.cu", "prngd_modes_fast.cu", "prngd_jump.cu",
            "prngd_mrg.cu", "prngd_convert.cu"]
+# (object, source, extra flags): one source compiled once per w
+VARIANTS = [(f"prngd_batch_modes_w{w}", "prngd_batch_modes.cu", [f"-DPRNGD_ANY_MODE_W={w}"]) for w in (32, 24, 0)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -47,16 +49,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(LIB_DIR, exist_ok=True)
     cc = nvcc()
 
-    def compile_one(src: str) -> str:
-        obj = os.path.join(OBJ_DIR, os.path.splitext(src)[0] + ".o")  # .cpp: host-only, same flags
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    units = [(os.path.splitext(src)[0], src, []) for src in SOURCES] + VARIANTS
+
+    def compile_one(unit) -> str:
+        name, src, extra = unit
+        obj = os.path.join(OBJ_DIR, name + ".o")  # .cpp: host-only, same flags
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.run(cmd, check=True)
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with ThreadPoolExecutor(max_workers=len(units)) as ex:
+        objs = list(ex.map(compile_one, units))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
     subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB_PATH)

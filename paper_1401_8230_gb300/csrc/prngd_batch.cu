@@ -30,8 +30,8 @@ struct BatchSlot {
   uint32_t* d_meta = nullptr;
   unsigned long long* d_ticket = nullptr;
   cudaEvent_t done = nullptr;
-  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};  // by kernel: mixed forms, A, B, C
-  int cfg_version[4] = {-1, -1, -1, -1};  // launch shape each graph was captured with
+  cudaGraphExec_t exec[5] = {};  // by kernel (kind + 2): any mode, mixed forms, A, B, C
+  int cfg_version[5] = {-1, -1, -1, -1, -1};  // launch shape each graph was captured with
   uint64_t ticket = 0;      // ticket of the batch last launched from this slot
 };
 
@@ -103,23 +103,15 @@ BatchShape default_batch_shape(int num_sms) {
 
 template <int W, int FORM_ALL>
 static cudaError_t launch_batch_wf(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
-  auto k = prngd::batch_kernel<W, FORM_ALL>;
-  const size_t smem = 1024 + (size_t)sh.warps_per_block * prngd::kTileBytes + 4 * (PRNG_MAX_BATCH_REQUESTS + 1);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const unsigned grid = (unsigned)(num_sms * sh.blocks_per_sm);
-  k<<<grid, sh.warps_per_block * 32, smem, s>>>(p);
-  return cudaGetLastError();
+  return prngd::launch_batch_kernel<W, FORM_ALL>(p, sh.warps_per_block, (unsigned)(num_sms * sh.blocks_per_sm),
+                                                 PRNG_MAX_BATCH_REQUESTS, s);
 }
 
 template <int W>
 static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, int form_all,
                                   cudaStream_t s) {
   switch (form_all) {
+    case prngd::kAnyMode: return launch_batch_any_mode_w<W>(p, sh, num_sms, s);
     case prngd::kFormA: return launch_batch_wf<W, prngd::kFormA>(p, sh, num_sms, s);
     case prngd::kFormB: return launch_batch_wf<W, prngd::kFormB>(p, sh, num_sms, s);
     case prngd::kFormC: return launch_batch_wf<W, prngd::kFormC>(p, sh, num_sms, s);
@@ -142,6 +134,16 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaS
   p.w = h->w;
   p.one = 1;
   p.items_per_ticket = (uint32_t)b->shape.items_per_ticket;
+  prngd::FillParams f4, f5;  // the map constants (Eq. 5 division, form A and form L factors)
+  set_mode_constants(f4, h->w, 0);
+  set_mode_constants(f5, h->w, PRNG_MODE_EQ5);
+  p.ec = f4.ec;
+  p.scale5 = f4.scale5;
+  p.k = f4.k;
+  p.l1_eq4 = f4.l1;
+  p.l2_eq4 = f4.l2;
+  p.l1_eq5 = f5.l1;
+  p.l2_eq5 = f5.l2;
   cudaError_t e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, form_all, s);
@@ -152,7 +154,7 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaS
 // Capture the slot's reset + launch once per launch shape.
 static int ensure_graph(prng_ctx* h, BatchSlot& sl, int form_all) {
   BatchEngine* b = h->batch;
-  const int g_i = form_all + 1;  // -1 (mixed) -> 0, A -> 1, B -> 2, C -> 3
+  const int g_i = form_all + 2;  // any mode -> 0, mixed forms -> 1, A -> 2, B -> 3, C -> 4
   if (sl.exec[g_i] && sl.cfg_version[g_i] == b->cfg_version) return PRNG_OK;
   if (sl.exec[g_i]) {
     cudaGraphExecDestroy(sl.exec[g_i]);
@@ -176,8 +178,12 @@ static int ensure_graph(prng_ctx* h, BatchSlot& sl, int form_all) {
 
 // Row layout of one request (see prng_request in prngd.h).
 static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
-  if (r.form != PRNG_FORM_A_FP64 && r.form != PRNG_FORM_B_INTBITS && r.form != PRNG_FORM_C_F32PAIR)
+  if (r.form != PRNG_FORM_A_FP64 && r.form != PRNG_FORM_B_INTBITS && r.form != PRNG_FORM_C_F32PAIR &&
+      r.form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "request form %d", r.form);
+  if (r.mode & ~(uint32_t)(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
+    return fail(PRNG_EINVAL, "request mode %u", r.mode);
+  d.mode = (uint16_t)r.mode;
   if (r.length == 0) return fail(PRNG_EINVAL, "request length 0");
   if (!r.d_out || ((uintptr_t)r.d_out & 15)) return fail(PRNG_EINVAL, "request d_out must be 16-byte aligned");
   d.length = r.length;
@@ -262,9 +268,13 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
     prngd::BatchDesc& q = sl->h_desc[i];
     if (q.full_rows < 32 || !encode_out_map(&sl->h_maps[i], q.out, q.full_rows, q.per_stream)) q.full_rows = 0;
   }
-  int form_all = d[0].form;  // one form for the whole batch selects a single-form kernel
+  // kernel: one form, mode 0 -> a single-form kernel; forms A, B, C, mode 0 -> the mixed-form
+  // kernel; otherwise the any-mode kernel
+  int form_all = d[0].form;
   for (int i = 1; i < n && form_all >= 0; ++i)
     if (d[i].form != form_all) form_all = -1;
+  for (int i = 0; i < n; ++i)
+    if (d[i].mode || d[i].form == PRNG_FORM_L_ALGO1) form_all = prngd::kAnyMode;
   rc = ensure_graph(h, *sl, form_all);
   if (rc) return rc;
   cudaError_t e = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(prngd::BatchDesc) * n, cudaMemcpyHostToDevice, s);
@@ -272,7 +282,7 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
     e = cudaMemcpyAsync(sl->d_maps, sl->h_maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl->d_meta, sl->h_meta, sizeof(uint32_t) * (n + 2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaGraphLaunch(sl->exec[form_all + 1], s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(sl->exec[form_all + 2], s);
   if (e == cudaSuccess) e = cudaEventRecord(sl->done, s);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "batch launch: %s", cudaGetErrorString(e));
   sl->ticket = b->next_ticket++;

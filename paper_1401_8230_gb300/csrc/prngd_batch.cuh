@@ -14,6 +14,8 @@
 
 namespace prngd {
 
+constexpr uint32_t kModeSingle = 4;  // BatchDesc::mode bit: Algorithm 1's single-redraw rejects
+
 struct BatchDesc {       // 64 bytes, built on the host
   uint64_t seed;         // fresh: seed of the streams
   uint64_t first_stream; // fresh: first stream id; resident: first handle stream
@@ -22,8 +24,9 @@ struct BatchDesc {       // 64 bytes, built on the host
   uint64_t* out;         // 16-byte aligned, length outputs
   uint64_t* rejects;     // nullable, one count per row
   uint32_t n_rows;       // streams used
-  int32_t form;          // kFormA / kFormB / kFormC
-  uint32_t resident;     // 1: rows continue handle streams
+  int32_t form;          // kFormA / kFormB / kFormC / kFormL
+  uint16_t resident;     // 1: rows continue handle streams
+  uint16_t mode;         // PRNG_MODE_* bits: Eq. 5 map, 1 - z, Algorithm 1's single redraw
   uint32_t full_rows;    // rows 0 .. full_rows-1 hold per_stream outputs and are covered by the
                          // request's tensor map (0: no map, plain stores only)
 };
@@ -40,6 +43,10 @@ struct BatchParams {
   int w;
   uint32_t one;
   uint32_t items_per_ticket;
+  DivConst ec;                    // Eq. 5: constants of D - 2
+  double scale5;                  // Eq. 5, form A: RN((1 - k^2)/(D - 2))
+  double k;                       // form L: 2^-w and its folded constants under Eq. 4 and Eq. 6
+  double l1_eq4, l2_eq4, l1_eq5, l2_eq5;
 };
 
 constexpr int kSlotPitch = 144;
@@ -65,20 +72,20 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
 // in a persistent launch, a fully unrolled chunk (eight pairs, each with its inline medium path)
 // no longer fits the instruction cache. Lane 0 waits for the warp's previous tensor store to
 // have read the tile before the first piece is written.
-template <int W, int FORM>
+template <int W, int FORM, int MAP>
 __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej, const FillParams& fp,
                                                  uint32_t my_row, uint32_t sw, int lane) {
 #pragma unroll 1
   for (uint32_t c = 0; c < (uint32_t)kChunk / 2; c += 2) {
     uint64_t a0, a1, b0, b1;
     if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
-      next_pair<W, FORM>(st, rej, fp, a0, a1);
-      next_pair<W, FORM>(st, rej, fp, b0, b1);
+      next_pair<W, FORM, MAP>(st, rej, fp, a0, a1);
+      next_pair<W, FORM, MAP>(st, rej, fp, b0, b1);
     } else {
-      a0 = next_output<W, FORM>(st, rej, fp);
-      a1 = next_output<W, FORM>(st, rej, fp);
-      b0 = next_output<W, FORM>(st, rej, fp);
-      b1 = next_output<W, FORM>(st, rej, fp);
+      a0 = next_output<W, FORM, MAP>(st, rej, fp);
+      a1 = next_output<W, FORM, MAP>(st, rej, fp);
+      b0 = next_output<W, FORM, MAP>(st, rej, fp);
+      b1 = next_output<W, FORM, MAP>(st, rej, fp);
     }
     if (c == 0) {  // warp-uniform
       if (lane == 0) bulk_wait_read<0>();
@@ -90,13 +97,19 @@ __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej,
 }
 
 // The conversion constants of a batch launch, as the fill code takes them.
-__device__ __forceinline__ FillParams fill_params_of(const BatchParams& bp) {
+template <int MAP = 0>
+__device__ __forceinline__ FillParams fill_params_of(const BatchParams& bp, uint32_t single = 0) {
   FillParams fp;
   fp.dc = bp.dc;
   fp.scale = bp.scale;
   fp.w = bp.w;
   fp.one = bp.one;
-  fp.single = 0;
+  fp.single = single;
+  fp.ec = bp.ec;
+  fp.scale5 = bp.scale5;
+  fp.k = bp.k;
+  fp.l1 = (MAP & kMapEq5) ? bp.l1_eq5 : bp.l1_eq4;
+  fp.l2 = (MAP & kMapEq5) ? bp.l2_eq5 : bp.l2_eq4;
   return fp;
 }
 
@@ -108,15 +121,15 @@ struct RowState {  // a row's stream and reject count, passed by value to out-of
 // Generates the lane's next min(left, kChunk) outputs (zeros after them) and stages them as
 // above; the whole chunk is written, after the same wait. Out of line: it runs once per row at
 // most, at the row's end. `bp` is the launch's grid constant.
-template <int W, int FORM>
-__device__ __noinline__ RowState stage_partial_chunk(RowState rs, const BatchParams& bp, uint32_t my_row,
-                                                     uint32_t sw, int lane, uint32_t left) {
-  const FillParams fp = fill_params_of(bp);
+template <int W, int FORM, int MAP>
+__device__ __noinline__ RowState stage_partial_chunk(RowState rs, const BatchParams& bp, uint32_t single,
+                                                     uint32_t my_row, uint32_t sw, int lane, uint32_t left) {
+  const FillParams fp = fill_params_of<MAP>(bp, single);
   XorShift128 st = rs.st;
   uint32_t rej = rs.rej;
   uint64_t v[kChunk];
 #pragma unroll
-  for (int j = 0; j < kChunk; ++j) v[j] = ((uint32_t)j < left) ? next_output<W, FORM>(st, rej, fp) : 0ull;
+  for (int j = 0; j < kChunk; ++j) v[j] = ((uint32_t)j < left) ? next_output<W, FORM, MAP>(st, rej, fp) : 0ull;
   if (lane == 0) bulk_wait_read<0>();
   __syncwarp();
 #pragma unroll
@@ -137,8 +150,8 @@ __device__ __forceinline__ XorShift128 item_row_state(const BatchDesc* __restric
 // An item of 32 full rows (every row holds per_stream outputs): rows row0 .. row0 + 31 of a
 // request, one per lane. Per chunk of 16 outputs the warp stages its 32 x 16 tile and lane 0
 // writes it with one 2D tensor store through the request's map (columns past per_stream are
-// clipped).
-template <int W, int FORM>
+// clipped). fp carries the request's reject rule.
+template <int W, int FORM, int MAP>
 __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
                                                 uint64_t row0, const BatchParams& bp, const FillParams& fp,
                                                 uint32_t tile, int lane) {
@@ -154,9 +167,9 @@ __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp
   for (uint32_t x0 = 0; x0 < per; x0 += kChunk) {
     const uint32_t left = per - x0;
     if (left >= (uint32_t)kChunk) {
-      stage_full_chunk<W, FORM>(st, rej, fp, my_row, sw, lane);
+      stage_full_chunk<W, FORM, MAP>(st, rej, fp, my_row, sw, lane);
     } else {
-      const RowState rs = stage_partial_chunk<W, FORM>(RowState{st, rej}, bp, my_row, sw, lane, left);
+      const RowState rs = stage_partial_chunk<W, FORM, MAP>(RowState{st, rej}, bp, fp.single, my_row, sw, lane, left);
       st = rs.st;
       rej = rs.rej;
     }
@@ -176,10 +189,11 @@ __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp
 // the hot loop above stays small. The warp stages the tile as above and stores it row by row:
 // lane (r, q) stores piece q of row k*4 + r, so each store instruction covers four 128-byte row
 // segments; rows are 16-byte aligned and a row's odd last output is stored as 8 bytes.
-template <int W, int FORM>
+template <int W, int FORM, int MAP>
 __device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp, uint64_t row0, const BatchParams& bp,
                                                uint32_t tile, int lane) {
-  const FillParams fp = fill_params_of(bp);
+  const uint32_t single = (dp->mode & kModeSingle) ? 1u : 0u;
+  const FillParams fp = fill_params_of<MAP>(bp, single);
   const uint64_t row = row0 + lane;
   const uint32_t n_rows = dp->n_rows;
   uint32_t count = 0;  // outputs of this lane's row (row length < 2^32, checked on the host)
@@ -200,9 +214,9 @@ __device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp,
   for (uint32_t x0 = 0; x0 < max_count; x0 += kChunk) {
     const uint32_t left = count > x0 ? count - x0 : 0u;
     if (__all_sync(0xffffffffu, left >= (uint32_t)kChunk)) {
-      stage_full_chunk<W, FORM>(st, rej, fp, my_row, sw, lane);
+      stage_full_chunk<W, FORM, MAP>(st, rej, fp, my_row, sw, lane);
     } else {
-      const RowState rs = stage_partial_chunk<W, FORM>(RowState{st, rej}, bp, my_row, sw, lane, left);
+      const RowState rs = stage_partial_chunk<W, FORM, MAP>(RowState{st, rej}, bp, single, my_row, sw, lane, left);
       st = rs.st;
       rej = rs.rej;
     }
@@ -230,20 +244,48 @@ __device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp,
   }
 }
 
-template <int W, int FORM>
+// fp: the launch's constants for MAP with the request's reject rule.
+template <int W, int FORM, int MAP = 0>
 __device__ __forceinline__ void batch_item(const BatchDesc* __restrict__ dp, const CUtensorMap* map, uint64_t row0,
                                            const BatchParams& bp, const FillParams& fp, uint32_t tile, int lane) {
   if (row0 + 32 <= dp->full_rows)  // warp-uniform
-    batch_item_full<W, FORM>(dp, map, row0, bp, fp, tile, lane);
+    batch_item_full<W, FORM, MAP>(dp, map, row0, bp, fp, tile, lane);
   else
-    batch_item_ragged<W, FORM>(dp, row0, bp, tile, lane);
+    batch_item_ragged<W, FORM, MAP>(dp, row0, bp, tile, lane);
+}
+
+// An item of a request with any form and map, out of line (one function per pair). Forms B
+// and C keep the w-specific fast paths at w = 32 and 24; forms A and L take the generic code,
+// as their fills do.
+template <int W, int FORM, int MAP>
+__device__ __noinline__ void batch_item_fm(const BatchDesc* __restrict__ dp, const CUtensorMap* map, uint64_t row0,
+                                           const BatchParams& bp, uint32_t tile, int lane) {
+  const FillParams fp = fill_params_of<MAP>(bp, (dp->mode & kModeSingle) ? 1u : 0u);
+  constexpr int WI = ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) ? W : 0;
+  batch_item<WI, FORM, MAP>(dp, map, row0, bp, fp, tile, lane);
+}
+
+template <int W, int FORM>
+__device__ __forceinline__ void batch_item_form_any_map(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
+                                                        uint64_t row0, const BatchParams& bp, uint32_t tile, int lane) {
+  switch (dp->mode & (kMapEq5 | kMapOneMinus)) {
+    case 0: batch_item_fm<W, FORM, 0>(dp, map, row0, bp, tile, lane); break;
+    case kMapEq5: batch_item_fm<W, FORM, kMapEq5>(dp, map, row0, bp, tile, lane); break;
+    case kMapOneMinus: batch_item_fm<W, FORM, kMapOneMinus>(dp, map, row0, bp, tile, lane); break;
+    default: batch_item_fm<W, FORM, kMapEq5 | kMapOneMinus>(dp, map, row0, bp, tile, lane); break;
+  }
 }
 
 // Persistent batch kernel: each warp repeatedly takes items_per_ticket items from the
 // counter. The per-request item prefix is copied into shared memory once per block; an item
 // is located by binary search there, or directly when it falls in the warp's last request.
-// FORM_ALL < 0: requests of any form (per-item switch); otherwise every request has FORM_ALL,
-// which keeps the code and its register footprint to one form.
+// FORM_ALL >= 0: every request has form FORM_ALL and mode 0 (Eq. 4, pair rejects), which keeps
+// the code and its register footprint to one form; -1: forms A, B and C with mode 0 (per-item
+// switch, inlined; form A converts on the FP64 pipe, see kFormAF); kAnyMode: any form and mode (per-item call of an out-of-line function).
+// In the first two the reject rule is fixed at compile time, so the hot loop carries the code
+// of one rule only.
+constexpr int kAnyMode = -2;
+
 template <int W, int FORM_ALL>
 __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ BatchParams bp) {
   extern __shared__ uint8_t smem_raw[];
@@ -276,11 +318,18 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
       }
       const BatchDesc* dp = bp.desc + r;
       const uint64_t row0 = (uint64_t)(item - prefix[r]) * 32;
-      if constexpr (FORM_ALL >= 0) {
+      if constexpr (FORM_ALL == kAnyMode) {
+        switch (dp->form) {
+          case kFormA: batch_item_form_any_map<W, kFormA>(dp, bp.maps + r, row0, bp, tile, lane); break;
+          case kFormC: batch_item_form_any_map<W, kFormC>(dp, bp.maps + r, row0, bp, tile, lane); break;
+          case kFormL: batch_item_form_any_map<W, kFormL>(dp, bp.maps + r, row0, bp, tile, lane); break;
+          default: batch_item_form_any_map<W, kFormB>(dp, bp.maps + r, row0, bp, tile, lane); break;
+        }
+      } else if constexpr (FORM_ALL >= 0) {
         batch_item<W, FORM_ALL>(dp, bp.maps + r, row0, bp, fp, tile, lane);
       } else {
         switch (dp->form) {
-          case kFormA: batch_item<W, kFormA>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          case kFormA: batch_item<W, kFormAF>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
           case kFormC: batch_item<W, kFormC>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
           default: batch_item<W, kFormB>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
         }
@@ -288,6 +337,22 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
     }
   }
   if (lane == 0) bulk_wait_all();
+}
+
+// Host: one launch of batch_kernel<W, FORM_ALL>, `blocks` blocks of `warps` warps; the
+// dynamic shared memory holds the warps' tiles and the item prefix of up to max_req requests.
+template <int W, int FORM_ALL>
+cudaError_t launch_batch_kernel(const BatchParams& p, int warps, unsigned blocks, int max_req, cudaStream_t s) {
+  auto k = batch_kernel<W, FORM_ALL>;
+  const size_t smem = 1024 + (size_t)warps * kTileBytes + 4 * ((size_t)max_req + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k<<<blocks, warps * 32, smem, s>>>(p);
+  return cudaGetLastError();
 }
 
 }  // namespace prngd

@@ -13,7 +13,11 @@ namespace prngd {
 constexpr int kChunk = 16;         // outputs per stream per staged tile (128 bytes per row)
 constexpr int kTileBytes = 32 * kChunk * 8;  // one warp: 32 streams x 16 outputs x 8 bytes
 
-enum Form : int { kFormA = 0, kFormB = 1, kFormC = 2, kFormL = 4 };
+enum Form : int { kFormA = 0, kFormB = 1, kFormC = 2, kFormL = 4, kFormAF = 8 };
+// kFormAF: form A's outputs, with RN(n) taken by the conversion instruction (FP64 pipe) instead of
+// integer rounding (ALU pipe). Alone, form A is faster with the integer rounding, since FP64
+// issue is scarce; beside the ALU-bound forms B and C in one kernel, the FP64 pipe is idle and
+// the conversion overlaps with their integer work.
 
 // Map bits (template parameter MAP of the per-output code): the map of Eq. 5 (one generator:
 // Eq. 6) instead of Eq. 4, and 1 - z instead of z. MAP = 0 is Eq. 4.
@@ -98,13 +102,17 @@ __device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, cons
   const int w = W > 0 ? W : p.w;
   if constexpr (FORM == kFormL) {
     return form_l_bits<MAP>(u1, u2, p);
-  } else if constexpr (FORM == kFormA) {
+  } else if constexpr (FORM == kFormA || FORM == kFormAF) {
     double z;
     if constexpr ((MAP & kMapEq5) != 0) {
       const uint64_t m = ((uint64_t)(u1 - 1u) << w) + u2;  // 0 for the pair mapped to z' = 0
-      z = __dmul_rn(__longlong_as_double((long long)(m ? u64_to_f64_bits(m) : 0ull)), p.scale5);  // RN(RN(m) C5)
+      const double rm = (FORM == kFormAF) ? __ull2double_rn(m)
+                                          : __longlong_as_double((long long)(m ? u64_to_f64_bits(m) : 0ull));
+      z = __dmul_rn(rm, p.scale5);  // RN(RN(m) C5)
     } else {
-      z = __dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(numerator(u1, u2, w))), p.scale);  // RN(RN(n) C_w)
+      const uint64_t n = numerator(u1, u2, w);
+      const double rn = (FORM == kFormAF) ? __ull2double_rn(n) : __longlong_as_double((long long)u64_to_f64_bits(n));
+      z = __dmul_rn(rn, p.scale);  // RN(RN(n) C_w)
     }
     if constexpr ((MAP & kMapOneMinus) != 0) z = __dsub_rn(1.0, z);
     return (uint64_t)__double_as_longlong(z);
@@ -141,7 +149,7 @@ template <int W, int FORM, int MAP = 0>
 __device__ __forceinline__ uint64_t next_output(XorShift128& st, uint32_t& rej, const FillParams& p) {
   const uint32_t u1 = draw<W>(st, p.w);
   const uint32_t u2 = draw<W>(st, p.w);
-  if constexpr (FORM == kFormA || FORM == kFormL) {
+  if constexpr (FORM == kFormA || FORM == kFormAF || FORM == kFormL) {
     const uint32_t top = (W == 32) ? 0xFFFFFFFFu : (W > 0 ? ((1u << W) - 1u) : ((1u << p.w) - 1u));
     if (__builtin_expect(accepted(u1, top), 1)) return convert_exact<W, FORM, MAP>(u1, u2, p);
     return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
@@ -510,6 +518,12 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
       if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
 #pragma unroll
         for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM, MAP>(st, rej, p, v[j], v[j + 1]);
+      } else if constexpr (FORM == kFormA) {
+        // one output in eight converts on the FP64 pipe (kFormAF), which the integer rounding
+        // leaves idle: measured 446 against 425 Gsamples/s for none (one in two: 352, in four: 401)
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j)
+          v[j] = (j % 8 == 0) ? next_output<W, kFormAF, MAP>(st, rej, p) : next_output<W, FORM, MAP>(st, rej, p);
       } else {
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) v[j] = next_output<W, FORM, MAP>(st, rej, p);

@@ -10,6 +10,7 @@
 
 namespace prngd {
 struct FillParams;
+struct BatchParams;
 }
 
 namespace prngd_host {
@@ -75,6 +76,16 @@ double scale_constant(const prngd::DivConst& dc);
 void set_mode_constants(prngd::FillParams& p, int w, int mode);
 void release_batch(prng_ctx* h);
 BatchShape default_batch_shape(int num_sms);
+// The batch kernel for requests of any form and mode at w = W (32, 24, or 0 for the generic
+// code); one translation unit defines each.
+template <int W>
+cudaError_t launch_batch_any_mode_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s);
+template <>
+cudaError_t launch_batch_any_mode_w<32>(const prngd::BatchParams&, const BatchShape&, int, cudaStream_t);
+template <>
+cudaError_t launch_batch_any_mode_w<24>(const prngd::BatchParams&, const BatchShape&, int, cudaStream_t);
+template <>
+cudaError_t launch_batch_any_mode_w<0>(const prngd::BatchParams&, const BatchShape&, int, cudaStream_t);
 int set_batch_shape(prng_ctx* h, const BatchShape& sh);
 int get_batch_shape(prng_ctx* h, BatchShape* sh);
 }  // namespace prngd_host

@@ -88,6 +88,7 @@ class Pool {
 struct Req {
   uint64_t client, length;
   int form;
+  uint32_t mode;
   size_t off, bytes;
   int state;  // 0 admitted, 1 launched, 2 done
   uint64_t ticket;
@@ -169,6 +170,7 @@ int launch_lane(prng_server* s, int lane) {
     prng_request q{};
     q.kind = PRNG_REQ_RESIDENT;
     q.form = r.form;
+    q.mode = r.mode;
     q.length = r.length;
     q.first_stream = r.client * s->S;
     q.n_streams = n;
@@ -247,12 +249,20 @@ int prng_server_destroy(prng_server_t s) {
 }
 
 int prng_server_submit(prng_server_t s, uint64_t client, uint64_t length, int form, uint64_t* id) {
+  return prng_server_submit_mode(s, client, length, form, 0, id);
+}
+
+int prng_server_submit_mode(prng_server_t s, uint64_t client, uint64_t length, int form, uint32_t mode,
+                            uint64_t* id) {
   if (!s || !id) return fail(PRNG_EINVAL, "null argument");
   if (client >= s->n_clients) return fail(PRNG_EINVAL, "client %llu of %llu", (unsigned long long)client,
                                           (unsigned long long)s->n_clients);
   if (length == 0) return fail(PRNG_EINVAL, "length 0");
-  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR)
+  if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR &&
+      form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "form %d", form);
+  if (mode & ~(uint32_t)(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
+    return fail(PRNG_EINVAL, "mode %u", mode);
   const size_t bytes = (size_t)length * 8;
   if (bytes > s->pool.size()) return fail(PRNG_EINVAL, "request larger than the whole pool");
   const size_t off = s->pool.alloc(bytes);
@@ -261,6 +271,7 @@ int prng_server_submit(prng_server_t s, uint64_t client, uint64_t length, int fo
   r.client = client;
   r.length = length;
   r.form = form;
+  r.mode = mode;
   r.off = off;
   r.bytes = bytes;
   r.state = 0;
@@ -344,7 +355,7 @@ int prng_server_run_trace(prng_server_t s, const prng_trace_item* items, uint64_
     while (!arrived.empty()) {  // admission in arrival order
       const uint64_t i = arrived.front();
       uint64_t id = 0;
-      int rc = prng_server_submit(s, items[i].client, items[i].length, items[i].form, &id);
+      int rc = prng_server_submit_mode(s, items[i].client, items[i].length, items[i].form, items[i].mode, &id);
       if (rc == PRNG_EBUSY) break;
       if (rc) return rc;
       ids[i] = id;
