@@ -532,7 +532,23 @@ def e2e(torch, P, g, samples_step):
     for _ in range(reps):
         g.fill_f64_host(host, PER_STREAM, P.FORM_B_INTBITS)
     dt = (time.perf_counter() - t0) / reps
-    del host
+    # the host link itself: plain device-to-pinned-host copies of the same bytes into the same
+    # buffer (copy engines; one stream, and four streams over quarters), best of three each
+    dev = torch.empty(samples_step, dtype=torch.float64, device="cuda")
+    best = float("inf")
+    for n_st in (1, 4):
+        streams = [torch.cuda.Stream() for _ in range(n_st)]
+        parts = list(zip(dev.chunk(n_st), host.chunk(n_st)))
+        for rep in range(4):  # the first round warms up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for st, (d, h) in zip(streams, parts):
+                with torch.cuda.stream(st):
+                    h.copy_(d, non_blocking=True)
+            torch.cuda.synchronize()
+            if rep:
+                best = min(best, time.perf_counter() - t0)
+    del dev, host
     # the same call into pageable memory (staged slices and copies), for comparison
     import numpy as np
 
@@ -542,18 +558,7 @@ def e2e(torch, P, g, samples_step):
     g.fill_f64_host(pageable, PER_STREAM, P.FORM_B_INTBITS)
     dt_pageable = time.perf_counter() - t0
     del pageable
-    # the host link itself: a plain device-to-pinned-host copy of the same bytes (copy engine)
-    dev = torch.empty(samples_step, dtype=torch.float64, device="cuda")
-    pinned = torch.empty(samples_step, dtype=torch.float64, pin_memory=True)
-    pinned.copy_(dev, non_blocking=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        pinned.copy_(dev, non_blocking=True)
-    torch.cuda.synchronize()
-    dt_copy = (time.perf_counter() - t0) / reps
-    del dev, pinned
-    link_gbs = samples_step * 8 / dt_copy / 1e9
+    link_gbs = samples_step * 8 / best / 1e9
     return {"value": samples_step / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": samples_step * 8, "ms_per_step": dt * 1e3,
             "api": "prng_fill_f64_host (pinned host buffer: direct device writes)",

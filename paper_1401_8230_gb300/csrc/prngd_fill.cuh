@@ -518,9 +518,10 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
       if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
 #pragma unroll
         for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM, MAP>(st, rej, p, v[j], v[j + 1]);
-      } else if constexpr (FORM == kFormA) {
+      } else if constexpr (FORM == kFormA && W == 32) {
         // one output in eight converts on the FP64 pipe (kFormAF), which the integer rounding
-        // leaves idle: measured 446 against 425 Gsamples/s for none (one in two: 352, in four: 401)
+        // leaves idle: measured 446 against 425 Gsamples/s for none (one in two: 352, in four:
+        // 401). Not at w = 24, where n < 2^53 converts exactly and cheaply (517 against 460).
 #pragma unroll
         for (int j = 0; j < kChunk; ++j)
           v[j] = (j % 8 == 0) ? next_output<W, kFormAF, MAP>(st, rej, p) : next_output<W, FORM, MAP>(st, rej, p);
