@@ -41,6 +41,11 @@ W = 32
 GAMMA = 0x9E3779B97F4A7C15
 PROFILE = os.path.join(ROOT, "profiles", "fill_b32_bulk_2p30.txt")
 KERNEL_SOURCES = ["paper_1401_8230_gb300/csrc/prngd_fill.cuh", "paper_1401_8230_gb300/csrc/prngd_math.cuh"]
+STATS_PROFILE = os.path.join(ROOT, "profiles", "stats_kernel_w32_fused.txt")
+STATS_SOURCES = ["paper_1401_8230_gb300/csrc/prngd_stats.cuh", "paper_1401_8230_gb300/csrc/prngd_math.cuh"]
+# the ALU pipe: 2 warp instructions (64 lanes) per clock per SM (ncu peak_sustained), 152 SMs,
+# 2.07 GHz maximum SM clock
+ALU_PEAK_GOPS = 152 * 64 * 2.07
 
 
 def shard_seed(seed: int, rank: int, n_streams: int) -> int:
@@ -70,25 +75,30 @@ def workload_desc():
             "l2": f"{N_STREAMS * PER_STREAM * 8 / 2**30:.2f} GiB output per step > 129 MB L2: no flush"}
 
 
-def kernel_hash():
+def kernel_hash(sources=None):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel."""
+def profiled_value(path, sources, key):
+    """A figure from a committed ncu summary, if the summary was taken on these kernel sources."""
     try:
-        text = open(PROFILE).read()
+        text = open(path).read()
     except OSError:
         return None
     m_h = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", text)
-    m_t = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_h or not m_t or m_h.group(1) != kernel_hash():
+    m_t = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m_h or not m_t or m_h.group(1) != kernel_hash(sources):
         return None
     return float(m_t.group(1))
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the bulk fill from its ncu summary."""
+    return profiled_value(PROFILE, KERNEL_SOURCES, "dram_bytes_per_launch")
 
 
 def load_peaks():
@@ -404,8 +414,15 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
     fn = lambda: gs.fused_stats(per, hist, sums, None, stream)  # noqa: E731
     fn()
     ms = sum(time_calls(torch, fn, 3, stream)) / 3
-    res["w32_fused_stats"] = {"gsamples_s": N_STREAMS * per / (ms * 1e-3) / 1e9, "ms": ms,
+    rate = N_STREAMS * per / (ms * 1e-3) / 1e9
+    res["w32_fused_stats"] = {"gsamples_s": rate, "ms": ms,
                               "outputs": N_STREAMS * per, "note": "2^20 streams x per_stream, no store"}
+    alu = profiled_value(STATS_PROFILE, STATS_SOURCES, "alu_warp_instructions_per_32_outputs")
+    if alu:  # ALU lane operations per output = ALU warp instructions per 32 outputs
+        res["w32_fused_stats"]["roofline"] = {
+            "bound": "alu", "achieved": rate * alu, "peak": ALU_PEAK_GOPS, "unit": "Gop/s",
+            "frac": rate * alu / ALU_PEAK_GOPS, "alu_ops_per_output": alu,
+            "peak_kind": "ALU pipe: 64 lanes per clock per SM x 152 SMs x 2.07 GHz (ncu peak_sustained, max clock)"}
     gs.close()
     return res
 
