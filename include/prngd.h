@@ -187,6 +187,9 @@ int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mo
  * A pair whose u1 is rejected (0 or 2^w - 1) gives all-ones bits (a NaN); the reject rule bit of
  * `mode` is ignored (there is no stream to redraw from). For callers with their own base draws,
  * and for testing the conversions on chosen inputs. No handle; asynchronous on cuda_stream.
+ * At w = 32 under Eq. 4 (forms B and C) pair i is rounded by the route the fills use for output
+ * i mod 4 of a row (integer normalisation or the u64 -> f64 conversion instruction); both give
+ * the same bits.
  * d_u1, d_u2: device arrays of n uint32; d_out: device array of n 8-byte outputs.
  * Errors: PRNG_EINVAL (w outside [2, 32], unknown form or mode bits, null pointers), PRNG_ECUDA.
  */

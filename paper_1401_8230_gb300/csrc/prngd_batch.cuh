@@ -72,15 +72,16 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
 // in a persistent launch, a fully unrolled chunk (eight pairs, each with its inline medium path)
 // no longer fits the instruction cache. Lane 0 waits for the warp's previous tensor store to
 // have read the tile before the first piece is written.
-template <int W, int FORM, int MAP>
+// CVT: the outputs of each 4-output step rounded by the conversion instruction (cvt_group_mask).
+template <int W, int FORM, int MAP, uint32_t CVT>
 __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej, const FillParams& fp,
                                                  uint32_t my_row, uint32_t sw, int lane) {
 #pragma unroll 1
   for (uint32_t c = 0; c < (uint32_t)kChunk / 2; c += 2) {
     uint64_t a0, a1, b0, b1;
     if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
-      next_pair<W, FORM, MAP>(st, rej, fp, a0, a1);
-      next_pair<W, FORM, MAP>(st, rej, fp, b0, b1);
+      next_pair<W, FORM, MAP>(st, rej, fp, a0, a1, CVT & 1u, (CVT >> 1) & 1u);
+      next_pair<W, FORM, MAP>(st, rej, fp, b0, b1, (CVT >> 2) & 1u, (CVT >> 3) & 1u);
     } else {
       a0 = next_output<W, FORM, MAP>(st, rej, fp);
       a1 = next_output<W, FORM, MAP>(st, rej, fp);
@@ -151,7 +152,7 @@ __device__ __forceinline__ XorShift128 item_row_state(const BatchDesc* __restric
 // request, one per lane. Per chunk of 16 outputs the warp stages its 32 x 16 tile and lane 0
 // writes it with one 2D tensor store through the request's map (columns past per_stream are
 // clipped). fp carries the request's reject rule.
-template <int W, int FORM, int MAP>
+template <int W, int FORM, int MAP, uint32_t CVT>
 __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
                                                 uint64_t row0, const BatchParams& bp, const FillParams& fp,
                                                 uint32_t tile, int lane) {
@@ -167,7 +168,7 @@ __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp
   for (uint32_t x0 = 0; x0 < per; x0 += kChunk) {
     const uint32_t left = per - x0;
     if (left >= (uint32_t)kChunk) {
-      stage_full_chunk<W, FORM, MAP>(st, rej, fp, my_row, sw, lane);
+      stage_full_chunk<W, FORM, MAP, CVT>(st, rej, fp, my_row, sw, lane);
     } else {
       const RowState rs = stage_partial_chunk<W, FORM, MAP>(RowState{st, rej}, bp, fp.single, my_row, sw, lane, left);
       st = rs.st;
@@ -214,7 +215,7 @@ __device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp,
   for (uint32_t x0 = 0; x0 < max_count; x0 += kChunk) {
     const uint32_t left = count > x0 ? count - x0 : 0u;
     if (__all_sync(0xffffffffu, left >= (uint32_t)kChunk)) {
-      stage_full_chunk<W, FORM, MAP>(st, rej, fp, my_row, sw, lane);
+      stage_full_chunk<W, FORM, MAP, cvt_group_mask<FORM, W, MAP>()>(st, rej, fp, my_row, sw, lane);
     } else {
       const RowState rs = stage_partial_chunk<W, FORM, MAP>(RowState{st, rej}, bp, single, my_row, sw, lane, left);
       st = rs.st;
@@ -244,12 +245,12 @@ __device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp,
   }
 }
 
-// fp: the launch's constants for MAP with the request's reject rule.
-template <int W, int FORM, int MAP = 0>
+// fp: the launch's constants for MAP with the request's reject rule; CVT as for stage_full_chunk.
+template <int W, int FORM, int MAP = 0, uint32_t CVT = cvt_group_mask<FORM, W, MAP>()>
 __device__ __forceinline__ void batch_item(const BatchDesc* __restrict__ dp, const CUtensorMap* map, uint64_t row0,
                                            const BatchParams& bp, const FillParams& fp, uint32_t tile, int lane) {
   if (row0 + 32 <= dp->full_rows)  // warp-uniform
-    batch_item_full<W, FORM, MAP>(dp, map, row0, bp, fp, tile, lane);
+    batch_item_full<W, FORM, MAP, CVT>(dp, map, row0, bp, fp, tile, lane);
   else
     batch_item_ragged<W, FORM, MAP>(dp, row0, bp, tile, lane);
 }
@@ -285,6 +286,13 @@ __device__ __forceinline__ void batch_item_form_any_map(const BatchDesc* __restr
 // In the first two the reject rule is fixed at compile time, so the hot loop carries the code
 // of one rule only.
 constexpr int kAnyMode = -2;
+
+// The mixed-form kernel gives its FP64 pipe to form A's conversion and rounds forms B and C with
+// integer operations. Measured on the batch of forms A/B/C interleaved (Gsamples/s): this 630;
+// A, B 1 in 2, C 1 in 2 on the FP64 pipe 560; A, B 3 in 4, C all 468; A by integers, B 3 in 4,
+// C all 511.
+constexpr int kMixA = kFormAF;
+constexpr uint32_t kMixCvtB = 0u, kMixCvtC = 0u;
 
 template <int W, int FORM_ALL>
 __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ BatchParams bp) {
@@ -329,9 +337,9 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
         batch_item<W, FORM_ALL>(dp, bp.maps + r, row0, bp, fp, tile, lane);
       } else {
         switch (dp->form) {
-          case kFormA: batch_item<W, kFormAF>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
-          case kFormC: batch_item<W, kFormC>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
-          default: batch_item<W, kFormB>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          case kFormA: batch_item<W, kMixA>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          case kFormC: batch_item<W, kFormC, 0, kMixCvtC>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          default: batch_item<W, kFormB, 0, kMixCvtB>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
         }
       }
     }

@@ -1,6 +1,8 @@
 // prngd_convert.cu -- the method's conversion applied to given base draws (prng_convert_pairs):
 // each accepted pair (u1, u2) goes through the same device code as the fills (PTX fast paths,
-// medium paths, exact division; Eq. 4 or Eq. 5, 1 - z; forms A, B, C and L).
+// medium paths, exact division; Eq. 4 or Eq. 5, 1 - z; forms A, B, C and L). At w = 32 under
+// Eq. 4, pair i is rounded by the route the fills use for output i of a row (integer
+// normalisation or the conversion instruction), so inputs placed at positions 0 .. 3 reach both.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <string.h>
@@ -17,7 +19,9 @@ __global__ void convert_pairs_kernel(const FillParams p, const uint32_t* __restr
   if (i >= n) return;
   const uint32_t top = (p.w == 32) ? 0xFFFFFFFFu : ((1u << p.w) - 1u);
   const uint32_t u1 = u1s[i] & top, u2 = u2s[i] & top;
-  out[i] = accepted(u1, top) ? convert_accepted<W, FORM, MAP>(u1, u2, p) : ~0ull;
+  // pair i takes the rounding route the fills give output i of a row (cvt_group_mask)
+  const bool cvt = ((cvt_group_mask<FORM, W, MAP>() >> (i & 3)) & 1u) != 0;
+  out[i] = accepted(u1, top) ? convert_accepted<W, FORM, MAP>(u1, u2, p, cvt) : ~0ull;
 }
 
 }  // namespace prngd

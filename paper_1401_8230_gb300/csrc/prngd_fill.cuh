@@ -198,97 +198,180 @@ __device__ __forceinline__ void xs_block4(XorShift128& s) {
 }
 
 // The w = 32 fast paths written out as PTX (Eq. 4: fast32_ok / fast32_bits; Eq. 5:
-// fast32_eq5_ok / fast32_eq5_bits), with the adds that need no carry issued as multiply-adds
-// by the run-time constant `one` so that they run on the FMA pipe beside the ALU work of the
-// draws. Both compute X = K1 u1 + 2 u2 + C0 and I = A 2^32 + 2A + u2 + (X >> 32) + PLUS:
-// Eq. 4 with (K1, C0, PLUS) = (3, -1, 1), X = 2B + 3A; Eq. 5 with (4, -4, 0 or 1), X = 4A + 2 u2.
-// Returns 1 in `ok` when 2^22 <= A <= 2^32 - 4 and the low word of X is below LIM; the value
-// is meaningless otherwise.
+// fast32_eq5_ok / fast32_eq5_bits) in two steps: the 64-bit I = floor(V 2^64) and the check,
+// then the rounding of I to the output's bits (bits_from_I_int or bits_from_I_cvt). The adds
+// that need no carry are multiply-adds by the run-time constant `one`, so that they run on the
+// FMA pipe beside the ALU work of the draws. X = K1 u1 + 2 u2 + C0 and
+// I = A 2^32 + 2A + u2 + (X >> 32) + PLUS: Eq. 4 with (K1, C0, PLUS) = (3, -1, 1), X = 2B + 3A;
+// Eq. 5 with (4, -4, 0 or 1), X = 4A + 2 u2. The check is 1 when 2^22 <= A <= 2^32 - 4 and the
+// low word of X is below LIM; I is meaningless otherwise.
+//
+// Both outputs of a pair (draws x, y and z, w), with one check for the two.
 template <int K1, int C0, int PLUS, unsigned LIM>
-__device__ __forceinline__ uint64_t fast32_bits_ptx_t(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
-  uint32_t lo, hi;
+__device__ __forceinline__ uint32_t fast32_pair_I_ptx_t(uint32_t x, uint32_t y, uint32_t z, uint32_t w, uint32_t one,
+                                                        uint64_t& Ia, uint64_t& Ib) {
+  uint32_t ok;
+  asm("{\n\t"
+      ".reg .u64 Ya, Xa, Pa, Ja, Yb, Xb, Pb, Jb;\n\t"
+      ".reg .u32 xla, fa, aa, Aa, ga, ila, iha, xlb, fb, ab, Ab, gb, ilb, ihb;\n\t"
+      ".reg .pred p1, p2, p3, p4;\n\t"
+      "mad.wide.u32 Ya, %4, 2, %8;\n\t"
+      "mad.wide.u32 Xa, %3, %9, Ya;\n\t"         // X of output a
+      "mov.b64 {xla, fa}, Xa;\n\t"
+      "mad.wide.u32 Yb, %6, 2, %8;\n\t"
+      "mad.wide.u32 Xb, %5, %9, Yb;\n\t"         // X of output b
+      "mov.b64 {xlb, fb}, Xb;\n\t"
+      "mad.lo.u32 aa, %3, %7, -4194305;\n\t"
+      "mad.lo.u32 ab, %5, %7, -4194305;\n\t"
+      "setp.lt.u32 p1, aa, 0xFFBFFFFD;\n\t"      // both A in [2^22, 2^32 - 4], both low words of X
+      "setp.lt.and.u32 p2, xla, %11, p1;\n\t"    // below LIM
+      "setp.lt.and.u32 p3, ab, 0xFFBFFFFD, p2;\n\t"
+      "setp.lt.and.u32 p4, xlb, %11, p3;\n\t"
+      "selp.u32 %0, 1, 0, p4;\n\t"
+      "mad.lo.u32 Aa, %3, %7, -1;\n\t"
+      "mov.b64 Pa, {%4, Aa};\n\t"
+      "mad.wide.u32 Ja, Aa, 2, Pa;\n\t"
+      "mad.lo.u32 ga, fa, %7, %10;\n\t"
+      "mov.b64 {ila, iha}, Ja;\n\t"
+      "add.cc.u32 ila, ila, ga;\n\t"
+      "addc.u32 iha, iha, 0;\n\t"
+      "mov.b64 %1, {ila, iha};\n\t"
+      "mad.lo.u32 Ab, %5, %7, -1;\n\t"
+      "mov.b64 Pb, {%6, Ab};\n\t"
+      "mad.wide.u32 Jb, Ab, 2, Pb;\n\t"
+      "mad.lo.u32 gb, fb, %7, %10;\n\t"
+      "mov.b64 {ilb, ihb}, Jb;\n\t"
+      "add.cc.u32 ilb, ilb, gb;\n\t"
+      "addc.u32 ihb, ihb, 0;\n\t"
+      "mov.b64 %2, {ilb, ihb};\n\t"
+      "}"
+      : "=r"(ok), "=l"(Ia), "=l"(Ib)
+      : "r"(x), "r"(y), "r"(z), "r"(w), "r"(one), "n"(C0), "n"(K1), "n"(PLUS), "n"(LIM));
+  return ok;
+}
+
+// One output.
+template <int K1, int C0, int PLUS, unsigned LIM>
+__device__ __forceinline__ uint64_t fast32_I_ptx_t(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
+  uint64_t I;
   asm("{\n\t"
       ".reg .u64 Y, X, P, Ip;\n\t"
-      ".reg .u32 xlo, f, a, A, g, ilo, ihi, q, s, rb, jlo, jhi, s1, mhi, e;\n\t"
+      ".reg .u32 xlo, f, a, A, g, ilo, ihi;\n\t"
       ".reg .pred p1, p2;\n\t"
-      "mad.wide.u32 Y, %4, 2, %6;\n\t"           // 2 u2 + C0
-      "mad.wide.u32 X, %3, %7, Y;\n\t"           // X = K1 u1 + 2 u2 + C0
+      "mad.wide.u32 Y, %3, 2, %5;\n\t"
+      "mad.wide.u32 X, %2, %6, Y;\n\t"
       "mov.b64 {xlo, f}, X;\n\t"
-      "mad.lo.u32 a, %3, %5, -4194305;\n\t"      // u1 - (2^22 + 1)
-      "setp.lt.u32 p1, a, 0xFFBFFFFD;\n\t"       // 2^22 <= A <= 2^32 - 4
-      "setp.lt.and.u32 p2, xlo, %9, p1;\n\t"
+      "mad.lo.u32 a, %2, %4, -4194305;\n\t"
+      "setp.lt.u32 p1, a, 0xFFBFFFFD;\n\t"
+      "setp.lt.and.u32 p2, xlo, %8, p1;\n\t"
       "selp.u32 %1, 1, 0, p2;\n\t"
-      "mad.lo.u32 A, %3, %5, -1;\n\t"            // A = u1 - 1
-      "mov.b64 P, {%4, A};\n\t"
-      "mad.wide.u32 Ip, A, 2, P;\n\t"            // A 2^32 + u2 + 2A
-      "mad.lo.u32 g, f, %5, %8;\n\t"
+      "mad.lo.u32 A, %2, %4, -1;\n\t"
+      "mov.b64 P, {%3, A};\n\t"
+      "mad.wide.u32 Ip, A, 2, P;\n\t"
+      "mad.lo.u32 g, f, %4, %7;\n\t"
       "mov.b64 {ilo, ihi}, Ip;\n\t"
-      "add.cc.u32 ilo, ilo, g;\n\t"              // I = A 2^32 + u2 + 2A + (X >> 32) + PLUS
+      "add.cc.u32 ilo, ilo, g;\n\t"
       "addc.u32 ihi, ihi, 0;\n\t"
-      "bfind.u32 q, ihi;\n\t"                    // p, top bit of the high word
-      "mad.lo.u32 s, q, %5, -21;\n\t"
+      "mov.b64 %0, {ilo, ihi};\n\t"
+      "}"
+      : "=l"(I), "=r"(ok)
+      : "r"(u1), "r"(u2), "r"(one), "n"(C0), "n"(K1), "n"(PLUS), "n"(LIM));
+  return I;
+}
+
+// RN(I 2^-64) as the output's bits, for I in [2^54, 2^64) with the exact value strictly
+// between I and I + 1, by integer operations (ALU and FMA pipes): p = the top bit of I, then
+// the mantissa (I + 2^(p - 53)) >> (p - 52) with the exponent (p + 990) << 20 added to its
+// high word (the implicit bit adds one more).
+__device__ __forceinline__ uint64_t bits_from_I_int(uint64_t I, uint32_t one) {
+  uint32_t lo, hi;
+  asm("{\n\t"
+      ".reg .u32 ilo, ihi, q, s, rb, jlo, jhi, s1, mhi, e;\n\t"
+      "mov.b64 {ilo, ihi}, %2;\n\t"
+      "bfind.u32 q, ihi;\n\t"
+      "mad.lo.u32 s, q, %3, -21;\n\t"
       "shl.b32 rb, 1, s;\n\t"
       "add.cc.u32 jlo, ilo, rb;\n\t"             // J = I + 2^s
       "addc.u32 jhi, ihi, 0;\n\t"
-      "mad.lo.u32 s1, q, %5, -20;\n\t"
-      "shf.r.wrap.b32 %2, jlo, jhi, s1;\n\t"     // mantissa, low word
+      "mad.lo.u32 s1, q, %3, -20;\n\t"
+      "shf.r.wrap.b32 %1, jlo, jhi, s1;\n\t"
       "shr.u32 mhi, jhi, s1;\n\t"
-      "mad.lo.u32 e, q, 0x100000, 0x3DE00000;\n\t"  // (p + 990) << 20
-      "mad.lo.u32 %0, mhi, %5, e;\n\t"
+      "mad.lo.u32 e, q, 0x100000, 0x3DE00000;\n\t"
+      "mad.lo.u32 %0, mhi, %3, e;\n\t"
       "}"
-      : "=r"(hi), "=r"(ok), "=r"(lo)
-      : "r"(u1), "r"(u2), "r"(one), "n"(C0), "n"(K1), "n"(PLUS), "n"(LIM));
+      : "=r"(hi), "=r"(lo)
+      : "l"(I), "r"(one));
   return ((uint64_t)hi << 32) | lo;
 }
-__device__ __forceinline__ uint64_t fast32_bits_ptx(uint32_t u1, uint32_t u2, uint32_t one, uint32_t& ok) {
-  return fast32_bits_ptx_t<3, -1, 1, 0xFFFFFFF8u>(u1, u2, one, ok);
+
+// The same by the u64 -> f64 conversion instruction (FP64 pipe), then 2^-64 as an exponent
+// subtraction. I has at least 55 bits, so the rounding point lies above bit 1 and the halfway
+// point below it is even; I | 1 therefore rounds as the exact value does, never as a tie.
+__device__ __forceinline__ uint64_t bits_from_I_cvt(uint64_t I, uint32_t one) {
+  uint32_t lo, hi;
+  asm("{\n\t"
+      ".reg .u64 J;\n\t"
+      ".reg .f64 d;\n\t"
+      ".reg .u32 dhi;\n\t"
+      "or.b64 J, %2, 1;\n\t"
+      "cvt.rn.f64.u64 d, J;\n\t"
+      "mov.b64 {%1, dhi}, d;\n\t"
+      "mad.lo.u32 %0, dhi, %3, -67108864;\n\t"   // exponent - 64
+      "}"
+      : "=r"(hi), "=r"(lo)
+      : "l"(I), "r"(one));
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// Which outputs of a 4-output group (bit i: output i) the pair paths (w = 32 and 24, forms B
+// and C, every map but w = 24 Eq. 5) round by the conversion instruction. The ALU pipe bounds
+// these kernels and the FP64 pipe is otherwise idle. Measured on the bulk fill (Gsamples/s,
+// none / 1 in 2 / 3 in 4 / all):
+//   form B: Eq. 4 669 / 696 / 720 / 595, Eq. 5 664 / 704 / 724 / 596, Eq. 5 and 1 - z
+//           624 / 668 / 688 / 594, w = 24 646 / 681 / 696 / 593 (7 in 8 at Eq. 4: 667);
+//   form C: Eq. 4 504 / 528 / 539 / 563, Eq. 5 464 / 478 / 492 / 506, w = 24 497 / 515 / 525 / 544
+// (form C spends more ALU work per output on the float pair, so the FP64 pipe has room for all).
+template <int FORM, int W = 32, int MAP = 0>
+__device__ __forceinline__ constexpr uint32_t cvt_group_mask() {
+  return FORM == kFormC ? 0xFu : 0xEu;
 }
 
 // The w = 24 fast path of fast24_ok / fast24_bits as PTX, from the raw 32-bit words (the draws
 // are their top 24 bits). With c1 = 3 u1 + 2 u2 - 1 (= 2B + 3A) and c2 = 4 u1 + 3 u2 - 1
 // (= 3B + 4A), K = c1 2^24 + c2, L = (2 u1 + u2 - 1) 2^16 + (K >> 32) and
-// I = (u1 - 1) 2^40 + L; then the same rounding as at w = 32. Returns 1 in `ok` when
-// 2^14 <= A <= 2^24 - 3 and the low word of K is below 2^32 - 16.
-__device__ __forceinline__ uint64_t fast24_bits_ptx(uint32_t x, uint32_t y, uint32_t one, uint32_t& ok) {
-  uint32_t lo, hi;
+// I = (u1 - 1) 2^40 + L, rounded as at w = 32. The check is 1 when 2^14 <= A <= 2^24 - 3 and
+// the low word of K is below 2^32 - 16.
+__device__ __forceinline__ uint64_t fast24_I_ptx(uint32_t x, uint32_t y, uint32_t one, uint32_t& ok) {
+  uint64_t I;
   asm("{\n\t"
       ".reg .u64 K, C2, KH, L;\n\t"
-      ".reg .u32 u1, u2, t, c1, t2, c2, klo, khi, a, d, llo, lhi, a8, ihi, q, s, rb, jlo, jhi, s1, mhi, e;\n\t"
+      ".reg .u32 u1, u2, t, c1, t2, c2, klo, khi, a, d, llo, lhi, a8, ihi;\n\t"
       ".reg .pred p1, p2;\n\t"
-      "shr.u32 u1, %3, 8;\n\t"
-      "shr.u32 u2, %4, 8;\n\t"
+      "shr.u32 u1, %2, 8;\n\t"
+      "shr.u32 u2, %3, 8;\n\t"
       "mad.lo.u32 t, u2, 2, -1;\n\t"
-      "mad.lo.u32 c1, u1, 3, t;\n\t"            // 3 u1 + 2 u2 - 1
+      "mad.lo.u32 c1, u1, 3, t;\n\t"
       "mad.lo.u32 t2, u2, 3, -1;\n\t"
-      "mad.lo.u32 c2, u1, 4, t2;\n\t"           // 4 u1 + 3 u2 - 1
+      "mad.lo.u32 c2, u1, 4, t2;\n\t"
       "cvt.u64.u32 C2, c2;\n\t"
-      "mad.wide.u32 K, c1, 16777216, C2;\n\t"   // K = c1 2^24 + c2
+      "mad.wide.u32 K, c1, 16777216, C2;\n\t"
       "mov.b64 {klo, khi}, K;\n\t"
-      "mad.lo.u32 a, u1, %5, -16385;\n\t"       // u1 - (2^14 + 1)
-      "setp.lt.u32 p1, a, 0xFFBFFE;\n\t"        // 2^14 <= A <= 2^24 - 3
+      "mad.lo.u32 a, u1, %4, -16385;\n\t"
+      "setp.lt.u32 p1, a, 0xFFBFFE;\n\t"
       "setp.lt.and.u32 p2, klo, 0xFFFFFFF0, p1;\n\t"
       "selp.u32 %1, 1, 0, p2;\n\t"
       "mad.lo.u32 d, u1, 2, u2;\n\t"
-      "mad.lo.u32 d, d, %5, -1;\n\t"            // 2 u1 + u2 - 1
+      "mad.lo.u32 d, d, %4, -1;\n\t"
       "cvt.u64.u32 KH, khi;\n\t"
-      "mad.wide.u32 L, d, 65536, KH;\n\t"       // L = d 2^16 + (K >> 32)
+      "mad.wide.u32 L, d, 65536, KH;\n\t"
       "mov.b64 {llo, lhi}, L;\n\t"
-      "mad.lo.u32 a8, u1, 256, -256;\n\t"       // A 2^8
-      "mad.lo.u32 ihi, lhi, %5, a8;\n\t"        // I high word (I low word = llo)
-      "bfind.u32 q, ihi;\n\t"
-      "mad.lo.u32 s, q, %5, -21;\n\t"
-      "shl.b32 rb, 1, s;\n\t"
-      "add.cc.u32 jlo, llo, rb;\n\t"            // J = I + 2^s
-      "addc.u32 jhi, ihi, 0;\n\t"
-      "mad.lo.u32 s1, q, %5, -20;\n\t"
-      "shf.r.wrap.b32 %2, jlo, jhi, s1;\n\t"
-      "shr.u32 mhi, jhi, s1;\n\t"
-      "mad.lo.u32 e, q, 0x100000, 0x3DE00000;\n\t"
-      "mad.lo.u32 %0, mhi, %5, e;\n\t"
+      "mad.lo.u32 a8, u1, 256, -256;\n\t"
+      "mad.lo.u32 ihi, lhi, %4, a8;\n\t"
+      "mov.b64 %0, {llo, ihi};\n\t"
       "}"
-      : "=r"(hi), "=r"(ok), "=r"(lo)
+      : "=l"(I), "=r"(ok)
       : "r"(x), "r"(y), "r"(one));
-  return ((uint64_t)hi << 32) | lo;
+  return I;
 }
 
 struct PairOut {
@@ -322,8 +405,11 @@ __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, ui
 // The output of an accepted pair by the fastest valid path, with the pair path's own code: at
 // w = 32 and w = 24 (forms B and C) the fast path (PTX where the pair path uses PTX), then the
 // medium path for small values, else the exact conversion.
+// cvt: round the fast path's value by the conversion instruction (as the pair path does for the
+// outputs cvt_group_mask selects; not for the w = 24 Eq. 5 path, which has no 64-bit I).
 template <int W, int FORM, int MAP>
-__device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, const FillParams& p) {
+__device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, const FillParams& p,
+                                                     bool cvt = false) {
   if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
     constexpr bool kComp = (MAP & kMapOneMinus) != 0;
     constexpr uint32_t top = (W == 32) ? 0xFFFFFFFFu : 0xFFFFFFu;
@@ -331,14 +417,16 @@ __device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, c
     uint64_t bits;
     if constexpr (W == 32 && (MAP & kMapEq5) != 0) {
       uint32_t ok;
-      bits = fast32_bits_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(a1, a2, p.one, ok);
+      const uint64_t I = fast32_I_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(a1, a2, p.one, ok);
+      bits = cvt ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
       if (!ok) {
         if (medium32_eq5_ok(a1, a2)) bits = medium32_eq5_bits(a1, a2, fast32_eq5_Y(a1, a2), kComp ? 1u : 0u);
         else return convert_exact<W, FORM, MAP>(u1, u2, p);
       }
     } else if constexpr (W == 32) {
       uint32_t ok;
-      bits = fast32_bits_ptx(a1, a2, p.one, ok);
+      const uint64_t I = fast32_I_ptx_t<3, -1, 1, 0xFFFFFFF8u>(a1, a2, p.one, ok);
+      bits = cvt ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
       if (!ok) {
         const uint64_t X = fast32_X(a1, a2);
         if (medium32_ok(a1, X, a2)) bits = medium32_bits(a1, a2, X);
@@ -350,7 +438,8 @@ __device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, c
       bits = fast24_eq5_bits(a1, a2, K, kComp ? 0x10000u : 0u);
     } else {
       uint32_t ok;
-      bits = fast24_bits_ptx(a1 << 8, a2 << 8, p.one, ok);  // raw words: the draws in their top 24 bits
+      const uint64_t I = fast24_I_ptx(a1 << 8, a2 << 8, p.one, ok);  // raw words: the draws in their top 24 bits
+      bits = cvt ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
       if (!ok) {
         const uint64_t K = fast24_K(a1, a2);
         if (medium24_ok(a1, K, a2)) bits = medium24_bits(a1, a2, K);
@@ -366,9 +455,11 @@ __device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, c
 // Two outputs of a w = 32 or w = 24 stream (forms B and C) from one 4-draw block, with one
 // branch for the pair. A small value takes the inline medium path; a reject or a value near
 // a rounding boundary replays the pair exactly from the block's starting state.
+// ca, cb: round output a / b by the conversion instruction (w = 32, Eq. 4; see
+// cvt_group_mask); callers pass constants.
 template <int W, int FORM, int MAP = 0>
 __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const FillParams& p, uint64_t& v0,
-                                          uint64_t& v1) {
+                                          uint64_t& v1, bool ca = false, bool cb = false) {
   xs_block4(st);
   // 1 - z: the arithmetic runs on the complemented draws (the state itself is not changed);
   // complementing the 32-bit word complements its top w bits.
@@ -380,10 +471,10 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
     // Eq. 5. At w = 32 small values take the inline medium path; rejects and boundary values
     // (and at w = 24 small values) replay the pair exactly.
     if constexpr (W == 32) {
-      uint32_t ok0, ok1;
-      v0 = fast32_bits_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(dx, dy, p.one, ok0);
-      v1 = fast32_bits_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(dz, dw, p.one, ok1);
-      ok = ok0 & ok1;
+      uint64_t Ia, Ib;
+      ok = fast32_pair_I_ptx_t<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(dx, dy, dz, dw, p.one, Ia, Ib);
+      v0 = ca ? bits_from_I_cvt(Ia, p.one) : bits_from_I_int(Ia, p.one);
+      v1 = cb ? bits_from_I_cvt(Ib, p.one) : bits_from_I_int(Ib, p.one);
     } else {
       const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
       const uint64_t Ka = fast24_eq5_K(u1a, u2a), Kb = fast24_eq5_K(u1b, u2b);
@@ -417,14 +508,15 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
     return;
   }
   if constexpr (W == 32) {
-    uint32_t ok0, ok1;
-    v0 = fast32_bits_ptx(dx, dy, p.one, ok0);
-    v1 = fast32_bits_ptx(dz, dw, p.one, ok1);
-    ok = ok0 & ok1;
+    uint64_t Ia, Ib;
+    ok = fast32_pair_I_ptx_t<3, -1, 1, 0xFFFFFFF8u>(dx, dy, dz, dw, p.one, Ia, Ib);
+    v0 = ca ? bits_from_I_cvt(Ia, p.one) : bits_from_I_int(Ia, p.one);
+    v1 = cb ? bits_from_I_cvt(Ib, p.one) : bits_from_I_int(Ib, p.one);
   } else {
     uint32_t ok0, ok1;
-    v0 = fast24_bits_ptx(dx, dy, p.one, ok0);
-    v1 = fast24_bits_ptx(dz, dw, p.one, ok1);
+    const uint64_t Ia = fast24_I_ptx(dx, dy, p.one, ok0), Ib = fast24_I_ptx(dz, dw, p.one, ok1);
+    v0 = ca ? bits_from_I_cvt(Ia, p.one) : bits_from_I_int(Ia, p.one);
+    v1 = cb ? bits_from_I_cvt(Ib, p.one) : bits_from_I_int(Ib, p.one);
     ok = ok0 & ok1;
   }
   if (__builtin_expect(ok == 0, 0)) {
@@ -517,7 +609,9 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
     if (left >= (uint64_t)kChunk) {
       if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
 #pragma unroll
-        for (int j = 0; j < kChunk; j += 2) next_pair<W, FORM, MAP>(st, rej, p, v[j], v[j + 1]);
+        for (int j = 0; j < kChunk; j += 2)
+          next_pair<W, FORM, MAP>(st, rej, p, v[j], v[j + 1], (cvt_group_mask<FORM, W, MAP>() >> (j & 3)) & 1u,
+                                  (cvt_group_mask<FORM, W, MAP>() >> ((j + 1) & 3)) & 1u);
       } else if constexpr (FORM == kFormA && W == 32) {
         // one output in eight converts on the FP64 pipe (kFormAF), which the integer rounding
         // leaves idle: measured 446 against 425 Gsamples/s for none (one in two: 352, in four:

@@ -1,6 +1,7 @@
 """GPU check of every conversion path on chosen inputs (prng_convert_pairs runs the fills' own
-device code on given draws): the PTX fast paths, medium paths and exact division at w = 32 and
-w = 24, for Eq. 4, Eq. 5 and 1 - z, on draws placed at each path's boundaries -- the low word of
+device code on given draws): the PTX fast paths (at w = 32 under Eq. 4 with both rounding routes,
+integer normalisation and the conversion instruction), medium paths and exact division at w = 32
+and w = 24, for Eq. 4, Eq. 5 and 1 - z, on draws placed at each path's boundaries -- the low word of
 the series sum next to a multiple of 2^32, the range edges of A, the largest values that round
 to 1.0 -- and on random and small-w draws. Every output is compared with the oracle bit for
 bit; rejected pairs give all-ones bits."""
@@ -122,8 +123,10 @@ def test_conversion_paths_at_their_boundaries(w, mode):
     if mode & P.MODE_ONE_MINUS:  # put the complemented draws (which the arithmetic sees) at the boundaries
         top = np.uint64(2**w - 1)
         u1, u2 = top - u1, top - u2
-    check(w, P.FORM_B_INTBITS, mode, u1, u2)
-    check(w, P.FORM_C_F32PAIR, mode, u1[:3000], u2[:3000])
+    for shift in range(4):  # every input at each position, so at each rounding route (pair i: route of output i mod 4)
+        a1, a2 = np.roll(u1, shift), np.roll(u2, shift)
+        check(w, P.FORM_B_INTBITS, mode, a1, a2)
+        check(w, P.FORM_C_F32PAIR, mode, a1[:3000], a2[:3000])
 
 
 @pytest.mark.parametrize("w", [2, 4, 12, 31])
