@@ -68,3 +68,34 @@ def test_eq5_medium_path_words_are_the_exact_floor(tmp_path):
         else:
             want = (2**64 - 1) * m * 2**96 // (D2 * 2**64)
         assert got == want, (u1, u2, plus)
+
+
+def test_conversion_route_rounds_like_the_exact_value():
+    """The fills round I = floor(V 2^64) either by integer normalisation (add half an ulp of I's
+    binade, truncate) or as RN(I | 1) by the u64 -> f64 conversion. For I in [2^54, 2^64) and an
+    exact value strictly between I and I + 1 (V is never dyadic), both equal RN of the exact value:
+    checked against correctly rounded rationals on the halfway points of every binade, their
+    neighbours and random values."""
+    import math
+    import random
+    from fractions import Fraction
+
+    def round_half_up(i):  # the integer route: I + 2^s truncated at bit s + 1 (s = p - 53)
+        s = i.bit_length() - 54
+        m = (i + (1 << s)) >> (s + 1)
+        return math.ldexp(float(m), s + 1)  # m has 53 bits (or 2^53 on carry): exact
+
+    rng = random.Random(1401)
+    cases = []
+    for p in range(54, 64):  # top bit p of I
+        s = p - 53
+        base = 1 << p
+        for k in (0, 1, 2, (1 << 53) - 1, rng.randrange(1 << 52)):
+            mid = base + (k << (s + 1)) + (1 << s)  # a halfway point of the binade
+            cases += [mid - 1, mid, mid + 1]
+        cases += [base, (base << 1) - 1] + [rng.randrange(base, base << 1) for _ in range(200)]
+    for i in cases:
+        for f in (Fraction(1, 2**70), Fraction(1, 3), Fraction(2**64 - 1, 2**64)):
+            exact = float(Fraction(i) + f)  # correctly rounded
+            assert float(i | 1) == exact, (i, f)
+            assert round_half_up(i) == exact, (i, f)
