@@ -207,11 +207,13 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
   CUtensorMap map;
   const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
   cudaError_t e;
-  const int map_bits = mode & (PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS);
+  // Fast kernels: w = 32 / 24, forms B and C, TMA stores; everything else: the generic ones,
+  // which have no conversion route (the same values by integer rounding).
+  const bool fast = mp && (h->w == 32 || h->w == 24) &&
+                    (form == PRNG_FORM_B_INTBITS || form == PRNG_FORM_C_F32PAIR);
+  int map_bits = map_bits_of(form, mode);
+  if (!fast) map_bits &= ~prngd::kMapCvt;
   if (map_bits || form == PRNG_FORM_L_ALGO1) {
-    // Fast kernels: w = 32 / 24, forms B and C, TMA stores; everything else: the generic ones.
-    const bool fast = mp && (h->w == 32 || h->w == 24) &&
-                      (form == PRNG_FORM_B_INTBITS || form == PRNG_FORM_C_F32PAIR);
     e = fast ? launch_fill_map_fast(p, form, map_bits, mp, s) : launch_fill_map(p, form, map_bits, mp, s);
     if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));
     return PRNG_OK;
@@ -339,8 +341,7 @@ int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mod
   if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR &&
       form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "unknown form %d", form);
-  if (mode & ~(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
-    return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
+  if (mode & ~kAllModes) return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
   if (per_stream == 0) return PRNG_OK;
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");

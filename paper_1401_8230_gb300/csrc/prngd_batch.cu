@@ -181,8 +181,7 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
   if (r.form != PRNG_FORM_A_FP64 && r.form != PRNG_FORM_B_INTBITS && r.form != PRNG_FORM_C_F32PAIR &&
       r.form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "request form %d", r.form);
-  if (r.mode & ~(uint32_t)(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
-    return fail(PRNG_EINVAL, "request mode %u", r.mode);
+  if (r.mode & ~(uint32_t)kAllModes) return fail(PRNG_EINVAL, "request mode %u", r.mode);
   d.mode = (uint16_t)r.mode;
   if (r.length == 0) return fail(PRNG_EINVAL, "request length 0");
   if (!r.d_out || ((uintptr_t)r.d_out & 15)) return fail(PRNG_EINVAL, "request d_out must be 16-byte aligned");

@@ -14,7 +14,8 @@
 
 namespace prngd {
 
-constexpr uint32_t kModeSingle = 4;  // BatchDesc::mode bit: Algorithm 1's single-redraw rejects
+constexpr uint32_t kModeSingle = 4;      // BatchDesc::mode bit: Algorithm 1's single-redraw rejects
+constexpr uint32_t kModeFp64Round = 8;   // BatchDesc::mode bit: form B's FP64 rounding route
 
 struct BatchDesc {       // 64 bytes, built on the host
   uint64_t seed;         // fresh: seed of the streams
@@ -269,6 +270,17 @@ __device__ __noinline__ void batch_item_fm(const BatchDesc* __restrict__ dp, con
 template <int W, int FORM>
 __device__ __forceinline__ void batch_item_form_any_map(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
                                                         uint64_t row0, const BatchParams& bp, uint32_t tile, int lane) {
+  if constexpr (FORM == kFormB) {
+    if (dp->mode & kModeFp64Round) {
+      switch (dp->mode & (kMapEq5 | kMapOneMinus)) {
+        case 0: batch_item_fm<W, FORM, kMapCvt>(dp, map, row0, bp, tile, lane); break;
+        case kMapEq5: batch_item_fm<W, FORM, kMapCvt | kMapEq5>(dp, map, row0, bp, tile, lane); break;
+        case kMapOneMinus: batch_item_fm<W, FORM, kMapCvt | kMapOneMinus>(dp, map, row0, bp, tile, lane); break;
+        default: batch_item_fm<W, FORM, kMapCvt | kMapEq5 | kMapOneMinus>(dp, map, row0, bp, tile, lane); break;
+      }
+      return;
+    }
+  }
   switch (dp->mode & (kMapEq5 | kMapOneMinus)) {
     case 0: batch_item_fm<W, FORM, 0>(dp, map, row0, bp, tile, lane); break;
     case kMapEq5: batch_item_fm<W, FORM, kMapEq5>(dp, map, row0, bp, tile, lane); break;

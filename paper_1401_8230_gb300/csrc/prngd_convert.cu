@@ -39,11 +39,21 @@ cudaError_t launch_convert(const prngd::FillParams& p, const uint32_t* u1, const
 template <int W, int FORM>
 cudaError_t by_map(int map, const prngd::FillParams& p, const uint32_t* u1, const uint32_t* u2, uint64_t n,
                    uint64_t* out, cudaStream_t s) {
-  switch (map) {
+  constexpr int E = prngd::kMapEq5, O = prngd::kMapOneMinus, V = prngd::kMapCvt;
+  if constexpr (FORM == prngd::kFormB) {  // form B's FP64 rounding route
+    switch (map) {
+      case V: return launch_convert<W, FORM, V>(p, u1, u2, n, out, s);
+      case V | E: return launch_convert<W, FORM, V | E>(p, u1, u2, n, out, s);
+      case V | O: return launch_convert<W, FORM, V | O>(p, u1, u2, n, out, s);
+      case V | E | O: return launch_convert<W, FORM, V | E | O>(p, u1, u2, n, out, s);
+      default: break;
+    }
+  }
+  switch (map & (E | O)) {
     case 0: return launch_convert<W, FORM, 0>(p, u1, u2, n, out, s);
-    case prngd::kMapEq5: return launch_convert<W, FORM, prngd::kMapEq5>(p, u1, u2, n, out, s);
-    case prngd::kMapOneMinus: return launch_convert<W, FORM, prngd::kMapOneMinus>(p, u1, u2, n, out, s);
-    default: return launch_convert<W, FORM, prngd::kMapEq5 | prngd::kMapOneMinus>(p, u1, u2, n, out, s);
+    case E: return launch_convert<W, FORM, E>(p, u1, u2, n, out, s);
+    case O: return launch_convert<W, FORM, O>(p, u1, u2, n, out, s);
+    default: return launch_convert<W, FORM, E | O>(p, u1, u2, n, out, s);
   }
 }
 
@@ -69,8 +79,7 @@ extern "C" int prng_convert_pairs(int w, int form, int mode, const uint32_t* d_u
   if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR &&
       form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "unknown form %d", form);
-  if (mode & ~(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
-    return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
+  if (mode & ~kAllModes) return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
   if (n == 0) return PRNG_OK;
   if (!d_u1 || !d_u2 || !d_out) return fail(PRNG_EINVAL, "null pointer");
   prngd::FillParams p;
@@ -80,7 +89,7 @@ extern "C" int prng_convert_pairs(int w, int form, int mode, const uint32_t* d_u
   p.w = w;
   p.one = 1;
   set_mode_constants(p, w, mode & (PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS));
-  const int map = mode & (PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS);
+  const int map = map_bits_of(form, mode);
   const cudaStream_t s = (cudaStream_t)cuda_stream;
   cudaError_t e;
   if (w == 32) e = by_form<32>(form, map, p, d_u1, d_u2, n, d_out, s);

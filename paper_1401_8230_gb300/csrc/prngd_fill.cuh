@@ -23,6 +23,9 @@ enum Form : int { kFormA = 0, kFormB = 1, kFormC = 2, kFormL = 4, kFormAF = 8 };
 // Eq. 6) instead of Eq. 4, and 1 - z instead of z. MAP = 0 is Eq. 4.
 constexpr int kMapEq5 = 1;
 constexpr int kMapOneMinus = 2;
+// Not a map: form B's rounding may use the FP64 conversion (PRNG_MODE_FP64_ROUND); the values
+// are the same, so only cvt_group_mask reads this bit.
+constexpr int kMapCvt = 4;
 
 struct FillParams {
   uint4* state;         // n_streams xorshift states (x, y, z, w)
@@ -324,7 +327,8 @@ __device__ __forceinline__ uint64_t bits_from_I_cvt(uint64_t I, uint32_t one) {
 }
 
 // Which outputs of a 4-output group (bit i: output i) the pair paths (w = 32 and 24, forms B
-// and C, every map but w = 24 Eq. 5) round by the conversion instruction. The ALU pipe bounds
+// and C, every map but w = 24 Eq. 5) round by the conversion instruction: form C all of them,
+// form B 3 in 4 when MAP has kMapCvt and none otherwise (form B is integer-only by default). The ALU pipe bounds
 // these kernels and the FP64 pipe is otherwise idle. Measured on the bulk fill (Gsamples/s,
 // none / 1 in 2 / 3 in 4 / all):
 //   form B: Eq. 4 669 / 696 / 720 / 595, Eq. 5 664 / 704 / 724 / 596, Eq. 5 and 1 - z
@@ -333,7 +337,7 @@ __device__ __forceinline__ uint64_t bits_from_I_cvt(uint64_t I, uint32_t one) {
 // (form C spends more ALU work per output on the float pair, so the FP64 pipe has room for all).
 template <int FORM, int W = 32, int MAP = 0>
 __device__ __forceinline__ constexpr uint32_t cvt_group_mask() {
-  return FORM == kFormC ? 0xFu : 0xEu;
+  return FORM == kFormC ? 0xFu : ((MAP & kMapCvt) ? 0xEu : 0x0u);
 }
 
 // The w = 24 fast path of fast24_ok / fast24_bits as PTX, from the raw 32-bit words (the draws

@@ -394,8 +394,7 @@ int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mo
   if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR &&
       form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "unknown form %d", form);
-  if (mode & ~(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
-    return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
+  if (mode & ~kAllModes) return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
   if (per_stream == 0) return PRNG_OK;
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");

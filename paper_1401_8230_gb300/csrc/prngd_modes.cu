@@ -34,7 +34,7 @@ cudaError_t launch_generic(const prngd::FillParams& p, const CUtensorMap* tmap, 
 
 template <int FORM>
 cudaError_t launch_form_map(const prngd::FillParams& p, int map, const CUtensorMap* tmap, cudaStream_t s) {
-  switch (map) {
+  switch (map & ~prngd::kMapCvt) {  // the generic code has no conversion route
     case 0: return launch_generic<FORM, 0>(p, tmap, s);
     case prngd::kMapEq5: return launch_generic<FORM, prngd::kMapEq5>(p, tmap, s);
     case prngd::kMapOneMinus: return launch_generic<FORM, prngd::kMapOneMinus>(p, tmap, s);

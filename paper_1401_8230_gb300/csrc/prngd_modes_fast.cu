@@ -1,6 +1,6 @@
 // prngd_modes_fast.cu -- fill kernels for the Eq. 5 and 1 - z maps (Section 2) at w = 32 and
-// w = 24, forms B and C: the pair fast paths of prngd_fill.cuh with the map as a template
-// parameter, TMA tile stores. Separate from prngd.cu so the instantiations compile in parallel.
+// w = 24, forms B and C, and form B's FP64 rounding route: the pair fast paths of
+// prngd_fill.cuh with the map as a template parameter, TMA tile stores. Separate from prngd.cu so the instantiations compile in parallel.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -29,13 +29,23 @@ cudaError_t launch_fast(const prngd::FillParams& p, const CUtensorMap* tmap, cud
 
 template <int W, int FORM>
 cudaError_t launch_map(const prngd::FillParams& p, int map, const CUtensorMap* tmap, cudaStream_t s) {
+  constexpr int E = prngd::kMapEq5, O = prngd::kMapOneMinus, V = prngd::kMapCvt;
   switch (map) {
-    case prngd::kMapEq5: return launch_fast<W, FORM, prngd::kMapEq5>(p, tmap, s);
-    case prngd::kMapOneMinus: return launch_fast<W, FORM, prngd::kMapOneMinus>(p, tmap, s);
-    case prngd::kMapEq5 | prngd::kMapOneMinus:
-      return launch_fast<W, FORM, prngd::kMapEq5 | prngd::kMapOneMinus>(p, tmap, s);
-    default: return cudaErrorInvalidValue;
+    case E: return launch_fast<W, FORM, E>(p, tmap, s);
+    case O: return launch_fast<W, FORM, O>(p, tmap, s);
+    case E | O: return launch_fast<W, FORM, E | O>(p, tmap, s);
+    default: break;
   }
+  if constexpr (FORM == prngd::kFormB) {  // form B's FP64 rounding route
+    switch (map) {
+      case V: return launch_fast<W, FORM, V>(p, tmap, s);
+      case V | E: return launch_fast<W, FORM, V | E>(p, tmap, s);
+      case V | O: return launch_fast<W, FORM, V | O>(p, tmap, s);
+      case V | E | O: return launch_fast<W, FORM, V | E | O>(p, tmap, s);
+      default: break;
+    }
+  }
+  return cudaErrorInvalidValue;
 }
 }  // namespace
 

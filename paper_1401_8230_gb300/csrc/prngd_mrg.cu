@@ -160,7 +160,9 @@ cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, 
 int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                     uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode) {
   if (n_streams == 0 || per_stream == 0) return PRNG_OK;
-  if (mode != 0 || (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR))
+  // PRNG_MODE_FP64_ROUND changes no value, and the MRG conversion has no such route: ignored
+  if ((mode & ~PRNG_MODE_FP64_ROUND) != 0 ||
+      (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR))
     return fail(PRNG_EINVAL, "MRG32k3a streams take forms A, B and C with mode 0");
   if (allow_tma && device_mapped_host(out, nullptr)) allow_tma = false;
   prngd::FillParams p;

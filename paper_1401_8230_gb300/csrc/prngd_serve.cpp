@@ -261,8 +261,7 @@ int prng_server_submit_mode(prng_server_t s, uint64_t client, uint64_t length, i
   if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR &&
       form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "form %d", form);
-  if (mode & ~(uint32_t)(PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW))
-    return fail(PRNG_EINVAL, "mode %u", mode);
+  if (mode & ~(uint32_t)prngd_host::kAllModes) return fail(PRNG_EINVAL, "mode %u", mode);
   const size_t bytes = (size_t)length * 8;
   if (bytes > s->pool.size()) return fail(PRNG_EINVAL, "request larger than the whole pool");
   const size_t off = s->pool.alloc(bytes);

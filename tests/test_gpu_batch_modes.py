@@ -101,6 +101,10 @@ def test_any_mode_batch_matches_the_oracle(w):
             mode = m | (P.MODE_SINGLE_REDRAW if (i + j) % 2 else 0)
             cases.append((L, chunk, form, mode))
     cases.append((64 * 70 + 13, 64, P.FORM_B_INTBITS, P.MODE_EQ5))
+    F = P.MODE_FP64_ROUND  # form B's FP64 rounding route: the oracle's values without the bit
+    cases += [(64 * 70 + 13, 64, P.FORM_B_INTBITS, F), (1025, 0, P.FORM_B_INTBITS, F | P.MODE_EQ5),
+              (40 * 48, 48, P.FORM_B_INTBITS, F | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW),
+              (999, 2, P.FORM_C_F32PAIR, F)]
     with P.Generator(3, 1, w) as g:
         run_fresh_batch(g, cases, w)
 
@@ -172,7 +176,7 @@ def test_mode_is_independent_of_the_batch_and_shape():
 def test_request_mode_errors():
     with P.Generator(1, 64, 32) as g:
         b = dev_buf(100)
-        for form, mode in [(3, 0), (5, 0), (P.FORM_B_INTBITS, 8)]:
+        for form, mode in [(3, 0), (5, 0), (P.FORM_B_INTBITS, 16)]:
             with pytest.raises(P.PrngError) as e:
                 P.prng_submit(g.h, [P.fresh_request(b, 10, 1, 0, form, 0, None, mode)])
             assert e.value.code == P.PRNG_EINVAL

@@ -18,6 +18,8 @@ import paper_1401_8230_gb300 as P  # noqa: E402
 OF = {P.FORM_A_FP64: O.FORM_A, P.FORM_B_INTBITS: O.FORM_B, P.FORM_C_F32PAIR: O.FORM_C, P.FORM_L_ALGO1: O.FORM_L}
 OM = {0: 0, P.MODE_EQ5: O.MODE_EQ5, P.MODE_ONE_MINUS: O.MODE_ONE_MINUS,
       P.MODE_EQ5 | P.MODE_ONE_MINUS: O.MODE_EQ5 | O.MODE_ONE_MINUS}
+F = P.MODE_FP64_ROUND  # form B's FP64 rounding route: the same values
+OM.update({F | k: v for k, v in list(OM.items())})
 
 
 def solve(rng, A_lo, A_hi, coefA, coefU, const, targets, count, u_max):
@@ -115,7 +117,8 @@ def check(w, form, mode, u1, u2):
     assert np.all(got[~acc] == np.uint64(2**64 - 1))
 
 
-@pytest.mark.parametrize("mode", [0, P.MODE_EQ5, P.MODE_ONE_MINUS, P.MODE_EQ5 | P.MODE_ONE_MINUS])
+@pytest.mark.parametrize("mode", [0, P.MODE_EQ5, P.MODE_ONE_MINUS, P.MODE_EQ5 | P.MODE_ONE_MINUS,
+                                  F, F | P.MODE_EQ5, F | P.MODE_ONE_MINUS])
 @pytest.mark.parametrize("w", [32, 24])
 def test_conversion_paths_at_their_boundaries(w, mode):
     eq5 = bool(mode & P.MODE_EQ5)

@@ -42,8 +42,12 @@ def same(a, b):
     return np.array_equal(np.ascontiguousarray(a).view(np.uint8), np.ascontiguousarray(b).view(np.uint8))
 
 
+# PRNG_MODE_FP64_ROUND changes no value (form B's rounding route only), so the oracle has no bit
+# for it: every case with it must equal the oracle's output without it.
+F = P.MODE_FP64_ROUND
 MODES = [P.MODE_EQ5, P.MODE_ONE_MINUS, P.MODE_EQ5 | P.MODE_ONE_MINUS, P.MODE_SINGLE_REDRAW,
-         P.MODE_EQ5 | P.MODE_SINGLE_REDRAW, P.MODE_EQ5 | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW]
+         P.MODE_EQ5 | P.MODE_SINGLE_REDRAW, P.MODE_EQ5 | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW,
+         F, F | P.MODE_EQ5, F | P.MODE_ONE_MINUS, F | P.MODE_EQ5 | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW]
 
 
 @pytest.mark.parametrize("w", [32, 24, 12])
@@ -64,7 +68,7 @@ def test_plain_store_path(form):
     """An odd per_stream and an output 8 bytes off a 16-byte boundary take the plain stores."""
     seed, ns, w = 31, 70, 32
     for per, offset in [(333, 0), (64, 1)]:
-        for mode in (P.MODE_EQ5, P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW):
+        for mode in (P.MODE_EQ5, P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW, F):
             with P.Generator(seed, ns, w) as g:
                 got, rej = run(g, per, form, mode, offset)
                 want, wrej = O.fill(seed, 0, ns, per, w, OF[form], omode(mode))
@@ -110,10 +114,22 @@ def test_mode_zero_is_the_plain_fill():
         assert torch.equal(x.view(torch.int64), y.view(torch.int64))
 
 
+@pytest.mark.parametrize("w", [32, 24, 17])
+def test_fp64_rounding_route_gives_form_b(w):
+    """Form B with PRNG_MODE_FP64_ROUND equals integer-only form B bit for bit (TMA and plain
+    stores; w = 17 has no such route and must ignore the bit); other forms ignore it."""
+    for per, offset in [(1024, 0), (333, 0), (64, 1)]:
+        for form in (P.FORM_B_INTBITS, P.FORM_C_F32PAIR, P.FORM_A_FP64):
+            with P.Generator(13, 256, w) as a, P.Generator(13, 256, w) as b:
+                x, rx = run(a, per, form, 0, offset)
+                y, ry = run(b, per, form, F, offset)
+                assert same(x, y) and np.array_equal(rx, ry), (w, per, offset, form)
+
+
 def test_bad_arguments():
     with P.Generator(1, 32, 32) as g:
         buf = torch.empty(32 * 16, dtype=torch.float64, device="cuda")
-        for form, mode in [(3, 0), (5, 0), (P.FORM_B_INTBITS, 8), (P.FORM_B_INTBITS, -1)]:
+        for form, mode in [(3, 0), (5, 0), (P.FORM_B_INTBITS, 16), (P.FORM_B_INTBITS, -1)]:
             with pytest.raises(P.PrngError) as e:
                 g.fill_mode(buf, 16, form, mode)
             assert e.value.code == P.PRNG_EINVAL
@@ -121,7 +137,7 @@ def test_bad_arguments():
             g.fill_f64(buf, 16, P.FORM_L_ALGO1)
 
 
-@pytest.mark.parametrize("mode", [P.MODE_EQ5, P.MODE_EQ5 | P.MODE_ONE_MINUS, P.MODE_ONE_MINUS])
+@pytest.mark.parametrize("mode", [P.MODE_EQ5, P.MODE_EQ5 | P.MODE_ONE_MINUS, P.MODE_ONE_MINUS, F, F | P.MODE_EQ5])
 def test_bulk_configuration_sampled(mode):
     """2^20 streams x 1024 outputs (8 GiB), w = 32, form B, in the launch the bench times; 48
     streams compared output by output with the oracle, all outputs inside the map's range."""
