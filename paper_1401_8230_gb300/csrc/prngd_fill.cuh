@@ -170,8 +170,9 @@ __device__ __forceinline__ uint64_t next_output(XorShift128& st, uint32_t& rej, 
         bits = fast32_eq5_bits(a1, a2, Y, kComp ? 1u : 0u);
       } else {
         const uint64_t K = fast24_eq5_K(a1, a2);
-        if (!__builtin_expect(fast24_eq5_ok(a1, K), 1)) return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
-        bits = fast24_eq5_bits(a1, a2, K, kComp ? 0x10000u : 0u);
+        if (__builtin_expect(fast24_eq5_ok(a1, K), 1)) bits = fast24_eq5_bits(a1, a2, K, kComp ? 0x10000u : 0u);
+        else if (medium24_eq5_ok(a1, a2)) bits = medium24_eq5_bits(a1, a2, kComp ? 1u : 0u);
+        else return slow_output<W, FORM, MAP>(u1, u2, st, rej, p);
       }
     } else if constexpr (W == 32) {
       const uint64_t X = fast32_X(a1, a2);
@@ -340,7 +341,7 @@ __device__ __forceinline__ uint32_t fast32_I_pair(uint32_t x, uint32_t y, uint32
 }
 
 // Which outputs of a 4-output group (bit i: output i) the pair paths (w = 32 and 24, forms B
-// and C, every map but w = 24 Eq. 5) round by the conversion instruction: form C all of them,
+// and C, every map) round by the conversion instruction: form C all of them,
 // form B 3 in 4 when MAP has kMapCvt and none otherwise (form B is integer-only by default). The ALU pipe bounds
 // these kernels and the FP64 pipe is otherwise idle. Measured on the bulk fill (Gsamples/s,
 // none / 1 in 2 / 3 in 4 / all):
@@ -423,7 +424,7 @@ __device__ __noinline__ PairOut slow_pair(uint32_t x, uint32_t y, uint32_t z, ui
 // w = 32 and w = 24 (forms B and C) the fast path (PTX where the pair path uses PTX), then the
 // medium path for small values, else the exact conversion.
 // cvt: round the fast path's value by the conversion instruction (as the pair path does for the
-// outputs cvt_group_mask selects; not for the w = 24 Eq. 5 path, which has no 64-bit I).
+// outputs cvt_group_mask selects).
 template <int W, int FORM, int MAP>
 __device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, const FillParams& p,
                                                      bool cvt = false) {
@@ -451,8 +452,14 @@ __device__ __forceinline__ uint64_t convert_accepted(uint32_t u1, uint32_t u2, c
       }
     } else if constexpr ((MAP & kMapEq5) != 0) {
       const uint64_t K = fast24_eq5_K(a1, a2);
-      if (!fast24_eq5_ok(a1, K)) return convert_exact<W, FORM, MAP>(u1, u2, p);
-      bits = fast24_eq5_bits(a1, a2, K, kComp ? 0x10000u : 0u);
+      if (fast24_eq5_ok(a1, K)) {
+        const uint64_t I = fast24_eq5_I(a1, a2, K, kComp ? 0x10000u : 0u);
+        bits = cvt ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
+      } else if (medium24_eq5_ok(a1, a2)) {
+        bits = medium24_eq5_bits(a1, a2, kComp ? 1u : 0u);
+      } else {
+        return convert_exact<W, FORM, MAP>(u1, u2, p);
+      }
     } else {
       uint32_t ok;
       const uint64_t I = fast24_I_ptx(a1 << 8, a2 << 8, p.one, ok);  // raw words: the draws in their top 24 bits
@@ -485,8 +492,8 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
   const uint32_t dz = kComp ? ~st.z : st.z, dw = kComp ? ~st.w : st.w;
   uint32_t ok;
   if constexpr ((MAP & kMapEq5) != 0) {
-    // Eq. 5. At w = 32 small values take the inline medium path; rejects and boundary values
-    // (and at w = 24 small values) replay the pair exactly.
+    // Eq. 5. Small values take the inline medium path (w = 32 and 24); rejects and boundary
+    // values replay the pair exactly.
     if constexpr (W == 32) {
       uint64_t Ia, Ib;
       ok = fast32_I_pair<4, -4, kComp ? 1 : 0, 0xFFFFFFC0u>(dx, dy, dz, dw, p.one, ca || cb, Ia, Ib);
@@ -496,11 +503,13 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
       const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
       const uint64_t Ka = fast24_eq5_K(u1a, u2a), Kb = fast24_eq5_K(u1b, u2b);
       ok = fast24_eq5_ok(u1a, Ka) & fast24_eq5_ok(u1b, Kb);
-      v0 = fast24_eq5_bits(u1a, u2a, Ka, kComp ? 0x10000u : 0u);
-      v1 = fast24_eq5_bits(u1b, u2b, Kb, kComp ? 0x10000u : 0u);
+      const uint64_t Ia = fast24_eq5_I(u1a, u2a, Ka, kComp ? 0x10000u : 0u);
+      const uint64_t Ib = fast24_eq5_I(u1b, u2b, Kb, kComp ? 0x10000u : 0u);
+      v0 = ca ? bits_from_I_cvt(Ia, p.one) : bits_from_I_int(Ia, p.one);
+      v1 = cb ? bits_from_I_cvt(Ib, p.one) : bits_from_I_int(Ib, p.one);
     }
     if (__builtin_expect(ok == 0, 0)) {
-      bool replay = W != 32;
+      bool replay = false;
       if constexpr (W == 32) {
         const uint64_t Ya = fast32_eq5_Y(dx, dy), Yb = fast32_eq5_Y(dz, dw);
         if (!fast32_eq5_ok(dx, Ya)) {
@@ -508,6 +517,14 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
         }
         if (!fast32_eq5_ok(dz, Yb)) {
           if (medium32_eq5_ok(dz, dw)) v1 = medium32_eq5_bits(dz, dw, Yb, kComp ? 1u : 0u); else replay = true;
+        }
+      } else {
+        const uint32_t u1a = dx >> 8, u2a = dy >> 8, u1b = dz >> 8, u2b = dw >> 8;
+        if (!fast24_eq5_ok(u1a, fast24_eq5_K(u1a, u2a))) {
+          if (medium24_eq5_ok(u1a, u2a)) v0 = medium24_eq5_bits(u1a, u2a, kComp ? 1u : 0u); else replay = true;
+        }
+        if (!fast24_eq5_ok(u1b, fast24_eq5_K(u1b, u2b))) {
+          if (medium24_eq5_ok(u1b, u2b)) v1 = medium24_eq5_bits(u1b, u2b, kComp ? 1u : 0u); else replay = true;
         }
       }
       if (replay) {

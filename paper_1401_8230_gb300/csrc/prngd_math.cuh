@@ -526,11 +526,44 @@ PRNGD_HD uint64_t fast24_eq5_K(uint32_t u1, uint32_t u2) {
 PRNGD_HD bool fast24_eq5_ok(uint32_t u1, uint64_t K) {
   return ((uint32_t)(u1 - 1u - 0x4000u) < 0xFFBFFEu) & ((uint32_t)K < 0xFFFFFFC0u);
 }
-PRNGD_HD uint64_t fast24_eq5_bits(uint32_t u1, uint32_t u2, uint64_t K, uint32_t plus) {
+// Medium path for Eq. 5 at w = 24 (1 <= A < 2^14, so m < 2^38). Exactly,
+//   (1 - 2^-48) / (1 - 2^-23 - 2^-48) = 1 + 2^-23 + 2^-46 + 2^-69 + 2^-71 + 2^-92 + 2^-93 + r,
+// 0 < r < 1.82 2^-115, so
+//   z' 2^96 = m 2^48 + m 2^25 + 4m + G / 2^45 + R,   G = m (2^24 + 2^22 + 3) < 2^63,
+// with 0 < R < 2^-28 for m < 2^38. floor(z' 2^96) is therefore the sum with floor(G / 2^45)
+// unless the low 45 bits of G lie within 2^20 of 2^45. The complement adds 2^-48, i.e. 2^48.
+PRNGD_HD bool medium24_eq5_ok(uint32_t u1, uint32_t u2) {
+  const uint64_t m = ((uint64_t)(u1 - 1u) << 24) + u2;
+  const uint64_t G = m * 0x1400003ull;
+  return ((uint32_t)(u1 - 2u) < 0x3FFFu) & ((G & 0x1FFFFFFFFFFFull) < 0x1FFFFFF00000ull);  // 1 <= A < 2^14
+}
+// The words t2 t1 t0 of floor(z' 2^96) (of the complement's, with plus = 1).
+PRNGD_HD void medium24_eq5_words(uint32_t u1, uint32_t u2, uint32_t plus, uint32_t& t2, uint32_t& t1,
+                                 uint32_t& t0) {
+  const uint64_t m = ((uint64_t)(u1 - 1u) << 24) + u2;
+  const uint64_t G = m * 0x1400003ull;
+  const uint64_t low = (m << 25) + 4u * m + (G >> 45) + ((uint64_t)plus << 48);  // < 2^64
+  const uint64_t lo64 = ((m & 0xFFFFull) << 48) + low;
+  t2 = (uint32_t)(m >> 16) + (lo64 < low ? 1u : 0u);
+  t1 = (uint32_t)(lo64 >> 32);
+  t0 = (uint32_t)lo64;
+}
+PRNGD_HD uint64_t medium24_eq5_bits(uint32_t u1, uint32_t u2, uint32_t plus) {
+  uint32_t t2, t1, t0;
+  medium24_eq5_words(u1, u2, plus, t2, t1, t0);
+  return rn_bits_from_scaled96(t2, t1, t0);
+}
+
+// I = floor(z' 2^64) of the w = 24 Eq. 5 fast path (>= 2^54 when fast24_eq5_ok holds).
+PRNGD_HD uint64_t fast24_eq5_I(uint32_t u1, uint32_t u2, uint64_t K, uint32_t plus) {
   const uint32_t A = u1 - 1u;
   const uint64_t L = ((uint64_t)(u2 + 2u * A) << 16) + (K >> 32) + plus;  // < 2^42
-  const uint32_t ilo = (uint32_t)L;
-  const uint32_t ihi = (A << 8) + (uint32_t)(L >> 32);  // >= 2^22
+  return ((uint64_t)((A << 8) + (uint32_t)(L >> 32)) << 32) | (uint32_t)L;
+}
+PRNGD_HD uint64_t fast24_eq5_bits(uint32_t u1, uint32_t u2, uint64_t K, uint32_t plus) {
+  const uint64_t I = fast24_eq5_I(u1, u2, K, plus);
+  const uint32_t ilo = (uint32_t)I;
+  const uint32_t ihi = (uint32_t)(I >> 32);  // >= 2^22
   const uint32_t p = 31u - (uint32_t)clz32(ihi);
   const uint32_t s = p - 21u;
   const uint32_t jlo = ilo + (1u << s);

@@ -56,18 +56,23 @@ static uint64_t want_rn(uint32_t u1, uint32_t u2, int w) { return bits_of(orc_va
 
 // "words" mode: for each line "u1 u2 plus" on stdin print the 96-bit words of the Eq. 5
 // medium path (t2 t1 t0), for an exact comparison with big-integer arithmetic.
-static int words_mode() {
+// "words24": the same for the w = 24 medium path.
+static int words_mode(bool w24) {
   unsigned long long a, b, c;
   while (scanf("%llu %llu %llu", &a, &b, &c) == 3) {
     uint32_t t2, t1, t0;
-    medium32_eq5_words((uint32_t)a, (uint32_t)b, fast32_eq5_Y((uint32_t)a, (uint32_t)b), (uint32_t)c, t2, t1, t0);
+    if (w24)
+      medium24_eq5_words((uint32_t)a, (uint32_t)b, (uint32_t)c, t2, t1, t0);
+    else
+      medium32_eq5_words((uint32_t)a, (uint32_t)b, fast32_eq5_Y((uint32_t)a, (uint32_t)b), (uint32_t)c, t2, t1, t0);
     printf("%u %u %u\n", t2, t1, t0);
   }
   return 0;
 }
 
 int main(int argc, char** argv) {
-  if (argc > 1 && strcmp(argv[1], "words") == 0) return words_mode();
+  if (argc > 1 && strcmp(argv[1], "words") == 0) return words_mode(false);
+  if (argc > 1 && strcmp(argv[1], "words24") == 0) return words_mode(true);
   std::mt19937_64 rng(2024);
   // 0. the compile-time division constants equal the ones derived at run time
   {
@@ -267,6 +272,23 @@ int main(int argc, char** argv) {
     expect(fast24_eq5_bits(u1, u2, K, 0), want_mode(u1, u2, 24, 1), "fast24_eq5 edge", u1, u2);
     expect(fast24_eq5_bits(u1, u2, K, 0x10000u), want_mode(0xFFFFFFu - u1, 0xFFFFFFu - u2, 24, 3),
            "fast24_eq5 edge 1-z", u1, u2);
+  }
+  // medium24_eq5: every small u1 class with random u2, and u2 placing the low 45 bits of
+  // G = m (2^24 + 2^22 + 3) next to 2^45 (checked where the medium path accepts)
+  for (int it = 0; it < 400000; ++it) {
+    const uint32_t u1 = 2u + (uint32_t)(rng() % 0x3FFFu);
+    uint32_t u2 = (uint32_t)(rng() & 0xFFFFFFu);
+    if (it & 1) {  // the u2 whose G mod 2^45 first reaches 2^45 - 2^20 - d on a random wrap j
+      const uint64_t c = 0x1400003ull, base = (((uint64_t)(u1 - 1u) << 24) * c) & 0x1FFFFFFFFFFFull;
+      const uint64_t t = (uint64_t)(rng() % 11) * (1ull << 45) + 0x1FFFFFF00000ull - (1u + rng() % (1u << 21));
+      if (t < base) continue;
+      const uint64_t v = (t - base + c - 1) / c;
+      if (v > 0xFFFFFFu) continue;
+      u2 = (uint32_t)v;
+    }
+    if (!medium24_eq5_ok(u1, u2)) continue;
+    expect(medium24_eq5_bits(u1, u2, 0), want_mode(u1, u2, 24, 1), "medium24_eq5", u1, u2);
+    expect(medium24_eq5_bits(u1, u2, 1), want_mode(0xFFFFFFu - u1, 0xFFFFFFu - u2, 24, 3), "medium24_eq5 1-z", u1, u2);
   }
   printf("checked %ld bad %ld\n", checked, bad);
   return bad != 0;

@@ -61,7 +61,7 @@ def boundary_pairs_w32(eq5):
 
 def boundary_pairs_w24(eq5):
     """At w = 24 the low words are found by brute force over all u2 for sampled u1 (Eq. 4) or by
-    solving for u2 modulo 2^30 (Eq. 5)."""
+    solving for u2 modulo 2^30 (Eq. 5); under Eq. 5 also pairs at the medium path's margin."""
     rng = np.random.default_rng(24 + eq5)
     M = 2**24 - 1
     u2all = np.arange(0, 2**24, dtype=np.uint64)
@@ -88,6 +88,16 @@ def boundary_pairs_w24(eq5):
         sel = sel[:200]
         u1s += [int(u1)] * len(sel)
         u2s += [int(v) for v in sel]
+    if eq5:  # the medium path (1 <= A < 2^14): G = m (2^24 + 2^22 + 3) with G mod 2^45 near its margin
+        c = 0x1400003
+        while len(u1s) < 6000:
+            u1 = int(rng.integers(2, 2**14 + 1))
+            m0 = (u1 - 1) * 2**24
+            t = int(rng.integers(0, 11)) * 2**45 + 2**45 - 2**20 - int(rng.integers(-2**22, 2**22)) - m0 * c % 2**45
+            if t < 0 or -(-t // c) >= 2**24:
+                continue
+            u1s.append(u1)
+            u2s.append(-(-t // c))
     edges1 = [1, 2, 2**14 - 1, 2**14, 2**14 + 1, 2**14 + 2, M - 3, M - 2, M - 1]
     edges2 = [0, 1, 2**23, M - 1, M]
     u1s += [x for x in edges1 for _ in edges2]

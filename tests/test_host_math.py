@@ -70,6 +70,44 @@ def test_eq5_medium_path_words_are_the_exact_floor(tmp_path):
         assert got == want, (u1, u2, plus)
 
 
+def test_eq5_medium_path_w24_words_are_the_exact_floor(tmp_path):
+    """The same for the w = 24 medium path: floor(z' 2^96) with z' = (1 - 2^-48) m / (D - 2),
+    m = (u1 - 1) 2^24 + u2, 1 <= u1 - 1 < 2^14 (the complement with plus = 1: + 2^48), on random
+    pairs and on pairs placing the low 45 bits of m (2^24 + 2^22 + 3) just below the path's
+    margin."""
+    import random
+    exe = build_check(tmp_path)
+    rng = random.Random(24)
+    D2 = (2**24 - 1) ** 2 - 2
+    cases = []
+    while len(cases) < 20000:
+        u1 = rng.randrange(2, 2**14 + 1)
+        m0 = (u1 - 1) * 2**24
+        if len(cases) % 2:  # G = m 0x1400003 with G mod 2^45 just below 2^45 - 2^20: u2 = ceil(t / c)
+            c = 0x1400003    # for t = j 2^45 + (2^45 - 2^20 - d) - m0 c, the u2 that just reaches it
+            t = rng.randrange(0, 11) * 2**45 + 2**45 - 2**20 - rng.randrange(1, 2**21) - m0 * c % 2**45
+            if t < 0:
+                continue
+            u2 = -(-t // c)
+            if u2 >= 2**24:
+                continue
+        else:
+            u2 = rng.randrange(0, 2**24)
+        m = m0 + u2
+        if (m * 0x1400003) % 2**45 >= 2**45 - 2**20:
+            continue  # outside the medium path
+        cases.append((u1, u2, rng.randrange(2)))
+    inp = "".join(f"{a} {b} {c}\n" for a, b, c in cases)
+    out = subprocess.run([str(exe), "words24"], input=inp, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0
+    for (u1, u2, plus), line in zip(cases, out.stdout.split("\n")):
+        t2, t1, t0 = (int(v) for v in line.split())
+        got = (t2 << 64) | (t1 << 32) | t0
+        m = (u1 - 1) * 2**24 + u2
+        want = ((2**48 - 1) * m * 2**96 + (D2 * 2**96 if plus else 0)) // (D2 * 2**48)
+        assert got == want, (u1, u2, plus)
+
+
 def test_conversion_route_rounds_like_the_exact_value():
     """The fills round I = floor(V 2^64) either by integer normalisation (add half an ulp of I's
     binade, truncate) or as RN(I | 1) by the u64 -> f64 conversion. For I in [2^54, 2^64) and an
