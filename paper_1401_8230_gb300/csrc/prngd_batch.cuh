@@ -77,8 +77,11 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
 template <int W, int FORM, int MAP, uint32_t CVT>
 __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej, const FillParams& fp,
                                                  uint32_t my_row, uint32_t sw, int lane) {
+  // my_row has zero bits 4..6 (1024-byte aligned tile, 128-byte rows): piece c lies at
+  // (my_row | (sw << 4)) ^ 16c, and the loop counts c4 = 16c
+  const uint32_t rowb = my_row | (sw << 4);
 #pragma unroll 1
-  for (uint32_t c = 0; c < (uint32_t)kChunk / 2; c += 2) {
+  for (uint32_t c4 = 0; c4 < (uint32_t)kChunk * 8u; c4 += 32u) {
     uint64_t a0, a1, b0, b1;
     if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
       next_pair<W, FORM, MAP>(st, rej, fp, a0, a1, CVT & 1u, (CVT >> 1) & 1u);
@@ -89,12 +92,12 @@ __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej,
       b0 = next_output<W, FORM, MAP>(st, rej, fp);
       b1 = next_output<W, FORM, MAP>(st, rej, fp);
     }
-    if (c == 0) {  // warp-uniform
+    if (c4 == 0) {  // warp-uniform
       if (lane == 0) bulk_wait_read<0>();
       __syncwarp();
     }
-    st_shared_v2(my_row + ((c ^ sw) << 4), a0, a1);
-    st_shared_v2(my_row + (((c + 1u) ^ sw) << 4), b0, b1);
+    st_shared_v2(rowb ^ c4, a0, a1);
+    st_shared_v2(rowb ^ c4 ^ 16u, b0, b1);
   }
 }
 

@@ -664,9 +664,11 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
     const uint32_t tile = tile0 + (chunk_idx % NBUF) * kTileBytes;
     if (lane == 0) bulk_wait_read<NBUF - 1>();
     __syncwarp();
+    // piece c at row + ((c ^ sw) << 4) = (row | (sw << 4)) ^ (c << 4): bits 4..6 of a row's
+    // address are zero (1024-byte aligned tiles, 128-byte rows), so one xor per store
+    const uint32_t rowb = (tile + row_off) | (sw << 4);
 #pragma unroll
-    for (int c = 0; c < kChunk / 2; ++c)
-      st_shared_v2(tile + row_off + (((uint32_t)c ^ sw) << 4), v[2 * c], v[2 * c + 1]);
+    for (int c = 0; c < kChunk / 2; ++c) st_shared_v2(rowb ^ ((uint32_t)c << 4), v[2 * c], v[2 * c + 1]);
     fence_async_shared();
     __syncwarp();
     if (lane == 0) {

@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(256) fill_mrg_tma_kernel(const FillParams p, c
     __syncwarp();
 #pragma unroll
     for (int c = 0; c < kChunk / 2; ++c)
-      st_shared_v2(tile + row_off + (((uint32_t)c ^ sw) << 4), v[2 * c], v[2 * c + 1]);
+      st_shared_v2(((tile + row_off) | (sw << 4)) ^ ((uint32_t)c << 4), v[2 * c], v[2 * c + 1]);  // as the fill
     fence_async_shared();
     __syncwarp();
     if (lane == 0) {
