@@ -510,6 +510,7 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates
     return {"requests": len(spec), "outputs": total, "placement": "256-byte aligned outputs in one pool",
             "gsamples_s": rate, "ms": ms, "vs_plain_fill": rate / plain_rate,
             "packed_16B": {"gsamples_s": packed, "ms": packed_ms, "vs_plain_fill": packed / plain_rate},
+            "kernel": "single-form (form B, FP64_ROUND)",
             "integer_only": {"gsamples_s": intb, "ms": int_ms, "kernel": "single-form",
                              "vs_plain_integer_only_fill": (intb / int_plain) if int_plain else None},
             "eq5_map": {"gsamples_s": eq5, "ms": eq5_ms, "kernel": "any-mode",

@@ -301,6 +301,9 @@ __device__ __forceinline__ void batch_item_form_any_map(const BatchDesc* __restr
 // In the first two the reject rule is fixed at compile time, so the hot loop carries the code
 // of one rule only.
 constexpr int kAnyMode = -2;
+// kFormBRound: every request is form B with exactly PRNG_MODE_FP64_ROUND (form B's values with
+// 3 of 4 outputs rounded on the FP64 pipe), in a single-form kernel like FORM_ALL = kFormB.
+constexpr int kFormBRound = 3;
 
 // The mixed-form kernel gives its FP64 pipe to form A's conversion and rounds forms B and C with
 // integer operations. Measured on the batch of forms A/B/C interleaved (Gsamples/s): this 630;
@@ -348,6 +351,8 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
           case kFormL: batch_item_form_any_map<W, kFormL>(dp, bp.maps + r, row0, bp, tile, lane); break;
           default: batch_item_form_any_map<W, kFormB>(dp, bp.maps + r, row0, bp, tile, lane); break;
         }
+      } else if constexpr (FORM_ALL == kFormBRound) {
+        batch_item<W, kFormB, kMapCvt>(dp, bp.maps + r, row0, bp, fp, tile, lane);
       } else if constexpr (FORM_ALL >= 0) {
         batch_item<W, FORM_ALL>(dp, bp.maps + r, row0, bp, fp, tile, lane);
       } else {

@@ -3,8 +3,9 @@ Eq. (5)/(6) map, 1 - z, Algorithm 1's single-redraw rejects) and form L (Algorit
 
 A request's mode changes only what each of its rows computes: the rows are the oracle's fill
 of the same streams with the same mode. Batches mix modes and forms, so every kernel the batch
-path selects is exercised: one form in mode 0 (single-form kernel), forms A/B/C in mode 0
-(mixed-form kernel), and any form and mode (any-mode kernel); full 32-row items
+path selects is exercised: one form in mode 0 (single-form kernel), form B with
+PRNG_MODE_FP64_ROUND alone (its single-form kernel), forms A/B/C in mode 0 (mixed-form kernel),
+and any form and mode (any-mode kernel); full 32-row items
 (tensor-map stores) and ragged ones, at w = 32, 24 and a small w where rejects are frequent."""
 import numpy as np
 import pytest
@@ -107,6 +108,25 @@ def test_any_mode_batch_matches_the_oracle(w):
               (999, 2, P.FORM_C_F32PAIR, F)]
     with P.Generator(3, 1, w) as g:
         run_fresh_batch(g, cases, w)
+
+
+@pytest.mark.parametrize("w", [32, 24, 5])
+def test_fp64_rounding_batches(w):
+    """Batches whose requests are all form B with PRNG_MODE_FP64_ROUND (their own single-form
+    kernel): fresh requests of every shape and resident requests give the oracle's form B."""
+    F = P.MODE_FP64_ROUND
+    with P.Generator(6, 1, w) as g:
+        run_fresh_batch(g, [(L, c, P.FORM_B_INTBITS, F) for L, c in SHAPES * 2], w)
+    seed, ns = 9, 96
+    with P.Generator(seed, ns, w) as g:
+        states = [O.stream_seed(seed, s) for s in range(ns)]
+        for first, n, L in [(0, 64, 64 * 33 + 16), (64, 32, 999)]:
+            b = dev_buf(L)
+            rej = torch.zeros(n, dtype=torch.int64, device="cuda")
+            P.prng_wait(g.h, P.prng_submit(g.h, [P.resident_request(b, L, first, n, P.FORM_B_INTBITS, rej, F)]), 60)
+            wv, wr, new = oracle_resident(states[first:first + n], L, w, P.FORM_B_INTBITS, 0)
+            assert same(as_host(b, L, P.FORM_B_INTBITS), wv) and np.array_equal(rej.cpu().numpy().astype(np.uint64), wr)
+            states[first:first + n] = new
 
 
 @pytest.mark.parametrize("w", [32, 24, 3])
