@@ -597,7 +597,7 @@ def e2e(torch, P, g, samples_step):
     link_gbs = samples_step * 8 / best / 1e9
     return {"value": samples_step / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": samples_step * 8, "ms_per_step": dt * 1e3,
-            "api": "prng_fill_f64_host (pinned host buffer: direct device writes)",
+            "api": "prng_fill_f64_host (pinned host buffer: device slices, copy-engine DMA)",
             "pageable_gsamples_s": samples_step / dt_pageable / 1e9,
             "host_link_copy_gbs": link_gbs,
             "host_link_frac": samples_step * 8 / dt / 1e9 / link_gbs}

@@ -207,11 +207,11 @@ int prng_convert_pairs(int w, int form, int mode, const uint32_t* d_u1, const ui
 
 /*
  * prng_fill_f64_host -- end-to-end fill into HOST memory: the same values as prng_fill_f64
- * (the streams advance identically) into `host_out` (n_streams * per_stream doubles). If
- * host_out is pinned (page-locked and mapped for the device), one kernel writes it directly
- * over the host link; otherwise the values are generated on the device in slices and copied
- * back, the next slice being generated while the previous one is copied. The call
- * synchronises. host_rejects (nullable, host memory) receives per-stream reject counts.
+ * (the streams advance identically) into `host_out` (n_streams * per_stream doubles). The
+ * values are generated on the device in slices (two 256 MiB staging buffers kept with the
+ * handle) and copied back by the copy engines, the next slice being generated while the
+ * previous one is copied; a pinned host_out is copied into directly at the host link's rate.
+ * The call synchronises. host_rejects (nullable, host memory) receives per-stream reject counts.
  * Errors: PRNG_EINVAL, PRNG_ENOMEM (staging buffers), PRNG_ECUDA.
  */
 int prng_fill_f64_host(prng_t h, double* host_out, uint64_t per_stream, int form,
