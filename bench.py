@@ -67,13 +67,13 @@ def max_over_ranks(dist, value: float, device) -> float:
 def workload_desc():
     if (N_STREAMS, PER_STREAM) == (1 << 20, 1024):
         name = ("bulk fill: 2^20 xorshift128 streams (seed 1) x 1024 outputs = 2^30 uniforms, "
-                "w=32, form B values (correctly rounded f64) with the FP64 rounding route "
+                "w=32, form B values (correctly rounded f64) by the balanced route "
                 "(3 of 4 outputs rounded by the u64->f64 conversion; integer-only form B in forms), "
                 "stream-major, 8 GiB, one launch")
     else:
         name = f"reduced bulk fill: {N_STREAMS} streams x {PER_STREAM} outputs, w=32, form B (profiling case)"
     return {"workload": name,
-            "n_streams": N_STREAMS, "per_stream": PER_STREAM, "w": W, "form": "B", "mode": "FP64_ROUND",
+            "n_streams": N_STREAMS, "per_stream": PER_STREAM, "w": W, "form": "B", "mode": "PRNG_MODE_BALANCED",
             "output": "f64",
             "l2": f"{N_STREAMS * PER_STREAM * 8 / 2**30:.2f} GiB output per step > 129 MB L2: no flush"}
 
@@ -286,7 +286,7 @@ def main():
     out = torch.empty(N_STREAMS * PER_STREAM, dtype=torch.float64, device="cuda")
 
     def step():
-        g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_FP64_ROUND, None, stream)
+        g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_BALANCED, None, stream)
 
     for _ in range(args.warmup):
         step()
@@ -339,7 +339,7 @@ def main():
     if rank == 0 and not args.no_batched:
         torch.cuda.empty_cache()
         forms = line.get("forms", {})
-        rates = {k: forms.get(k, {}).get("gsamples_s") for k in ("w32_formB_intbits", "w32_eq5_formB_fp64_round")}
+        rates = {k: forms.get(k, {}).get("gsamples_s") for k in ("w32_formB_intbits", "w32_eq5_formB_balanced")}
         line["batched"] = batched(torch, P, stream, plain_rate, args.batched_requests, args.batched_hi,
                                   not args.no_autotune, rates)
         torch.cuda.empty_cache()
@@ -373,12 +373,14 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
 
     for name, fn in [
         ("w32_formA_fp64", lambda: g.fill_f64(out, PER_STREAM, P.FORM_A_FP64, None, stream)),
+        ("w32_formA_balanced",
+         lambda: g.fill_mode(out, PER_STREAM, P.FORM_A_FP64, P.MODE_BALANCED, None, stream)),
         ("w32_formB_intbits", lambda: g.fill_f64(out, PER_STREAM, P.FORM_B_INTBITS, None, stream)),
         ("w32_formC_f32pair", lambda: g.fill_f32pair(out, PER_STREAM, None, stream)),
         # Section 2's other maps and Algorithm 1's literal FP64 evaluation
         ("w32_eq5_formB", lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_EQ5, None, stream)),
-        ("w32_eq5_formB_fp64_round",
-         lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_EQ5 | P.MODE_FP64_ROUND, None, stream)),
+        ("w32_eq5_formB_balanced",
+         lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_EQ5 | P.MODE_BALANCED, None, stream)),
         ("w32_one_minus_formB", lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_ONE_MINUS, None, stream)),
         ("w32_eq5_one_minus_formB",
          lambda: g.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_EQ5 | P.MODE_ONE_MINUS, None, stream)),
@@ -391,7 +393,7 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
     # a few long streams: 64 streams x 2^24 outputs (the same 2^30 outputs), cut into pieces by
     # jump-ahead so that they fill the GPU (prng_fill_split, automatic piece count)
     gl = P.Generator(SEED, 64, W)
-    fn = lambda: gl.fill_split(out, n // 64, P.FORM_B_INTBITS, P.MODE_FP64_ROUND, 0, None, stream)  # noqa: E731
+    fn = lambda: gl.fill_split(out, n // 64, P.FORM_B_INTBITS, P.MODE_BALANCED, 0, None, stream)  # noqa: E731
     fn()
     ms = sum(time_calls(torch, fn, reps, stream)) / reps
     res["w32_split_64_streams_formB"] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak,
@@ -407,8 +409,9 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
     gm.close()
     g24 = P.Generator(SEED, N_STREAMS, 24)
     for name, form, mode in [("w24_formB_intbits", P.FORM_B_INTBITS, 0),
-                             ("w24_formB_fp64_round", P.FORM_B_INTBITS, P.MODE_FP64_ROUND),
-                             ("w24_formA_fp64", P.FORM_A_FP64, 0)]:
+                             ("w24_formB_balanced", P.FORM_B_INTBITS, P.MODE_BALANCED),
+                             ("w24_formA_fp64", P.FORM_A_FP64, 0),
+                             ("w24_formA_balanced", P.FORM_A_FP64, P.MODE_BALANCED)]:
         fn = lambda form=form, mode=mode: g24.fill_mode(out, PER_STREAM, form, mode, None, stream)  # noqa: E731
         fn()
         ms = sum(time_calls(torch, fn, reps, stream)) / reps
@@ -440,7 +443,7 @@ TUNE_TABLE = os.path.join(ROOT, "paper_1401_8230_gb300", "lib", "autotune.txt")
 
 def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates=None):
     """4096 fresh requests, log-uniform lengths in [2^8, 2^26], own seeds and stream offsets,
-    w = 32 form B with the FP64 rounding route (as the bench step), one persistent launch (graph
+    w = 32 form B by the balanced route (as the bench step), one persistent launch (graph
     replay) with the autotuned shape; against the same requests as 4096 single-request
     launches. Each request's output starts on a 256-byte boundary of one pool (as separately
     allocated outputs would). Also timed: the same batch packed at 16-byte offsets, with
@@ -452,7 +455,7 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates
     total = sum(r["length"] for r in spec)
     g = P.Generator(SEED, 1, W)
     tuned = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, hi, TUNE_TABLE) if tune else None
-    F = P.MODE_FP64_ROUND
+    F = P.MODE_BALANCED
 
     def place(align, mode=0):
         """One pool, request i at a multiple of `align` outputs; returns (pool, request array)."""
@@ -506,11 +509,11 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates
     packed = total / (packed_ms * 1e-3) / 1e9
     eq5 = total / (eq5_ms * 1e-3) / 1e9
     intb = total / (int_ms * 1e-3) / 1e9
-    int_plain, eq5_plain = rates.get("w32_formB_intbits"), rates.get("w32_eq5_formB_fp64_round")
+    int_plain, eq5_plain = rates.get("w32_formB_intbits"), rates.get("w32_eq5_formB_balanced")
     return {"requests": len(spec), "outputs": total, "placement": "256-byte aligned outputs in one pool",
             "gsamples_s": rate, "ms": ms, "vs_plain_fill": rate / plain_rate,
             "packed_16B": {"gsamples_s": packed, "ms": packed_ms, "vs_plain_fill": packed / plain_rate},
-            "kernel": "single-form (form B, FP64_ROUND)",
+            "kernel": "single-form (form B, PRNG_MODE_BALANCED)",
             "integer_only": {"gsamples_s": intb, "ms": int_ms, "kernel": "single-form",
                              "vs_plain_integer_only_fill": (intb / int_plain) if int_plain else None},
             "eq5_map": {"gsamples_s": eq5, "ms": eq5_ms, "kernel": "any-mode",

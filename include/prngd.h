@@ -49,10 +49,11 @@ extern "C" {
 #define PRNG_ENOTFOUND 6 /* unknown ticket                                                  */
 
 /* Output forms. All three are functions of the same accepted n; each output is 8 bytes. */
-#define PRNG_FORM_A_FP64 0    /* double RN(RN(n) * C_w), C_w = RN(1/D): the FP64 sequence;  */
-                              /* at most 1 ulp from RN(n/D)                                 */
+#define PRNG_FORM_A_FP64 0    /* double RN(RN(n) * C_w), C_w = RN(1/D): the FP64 sequence   */
+                              /* (u64 -> f64 conversion, multiply); at most 1 ulp from      */
+                              /* RN(n/D) (see PRNG_MODE_BALANCED)                            */
 #define PRNG_FORM_B_INTBITS 1 /* double RN(n/D), correctly rounded, built with integer ops  */
-                              /* only (see PRNG_MODE_FP64_ROUND)                          */
+                              /* only (see PRNG_MODE_BALANCED)                          */
 #define PRNG_FORM_C_F32PAIR 2 /* two floats (hi, lo): hi = RN32(d), lo = RN32(d - hi), with */
                               /* d the form-B value; stored interleaved hi, lo               */
 #define PRNG_FORM_L_ALGO1 4   /* double: Algorithm 1's Z evaluated literally in FP64, one IEEE */
@@ -63,8 +64,8 @@ extern "C" {
                                     /* (n - 1)/(D - 2), range [0, 1 - k^2] with k = 2^-w        */
 #define PRNG_MODE_ONE_MINUS 2       /* output 1 - z' instead of z' (Section 2: excludes zero)  */
 #define PRNG_MODE_SINGLE_REDRAW 4   /* Algorithm 1's reject loop: redraw only r1, then draw r2  */
-#define PRNG_MODE_FP64_ROUND 8      /* form B: the same bits, with the last rounding of 3 in 4  */
-                                    /* outputs done by the FP64 pipe's u64 -> f64 conversion    */
+#define PRNG_MODE_BALANCED 8        /* forms A and B: the same bits by a route that shares the  */
+                                    /* work between the integer and FP64 pipes                  */
 
 typedef struct prng_ctx* prng_t;
 
@@ -148,12 +149,13 @@ int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_r
  *    Eq. 4 it equals z' of the complemented draws); forms A and L: one more FP64 subtraction.
  *  - PRNG_MODE_SINGLE_REDRAW (Algorithm 1): a rejected r1 is redrawn alone and r2 is drawn
  *    after the accepted r1; d_rejects then counts redrawn r1 values.
- *  - PRNG_MODE_FP64_ROUND: form B's values, unchanged, by a faster route. Form B builds the
- *    correctly rounded double with integer instructions only; with this bit, 3 of every 4
- *    outputs of a row (w = 32 and 24) take I = floor(V 2^64) to double by the u64 -> f64
- *    conversion instead (as RN(I | 1), the same rounding), which balances the integer and FP64
- *    pipes. No effect on the other forms (form C always rounds this way; it has no
- *    integer-only requirement).
+ *  - PRNG_MODE_BALANCED: the same values by a faster route that balances the integer and
+ *    FP64 pipes. Form B builds the correctly rounded double with integer instructions only;
+ *    with this bit, 3 of every 4 outputs of a row (w = 32 and 24) take I = floor(V 2^64) to
+ *    double by the u64 -> f64 conversion instead (as RN(I | 1), the same rounding). Form A
+ *    takes RN(n) by the conversion instruction; with this bit, by integer rounding (exact, the
+ *    same double) for 7 of every 8 outputs at w = 32 and all at other w. No effect on forms C
+ *    (which always rounds on the FP64 pipe; it has no integer-only definition) and L.
  * Form L with PRNG_MODE_SINGLE_REDRAW is Algorithm 1 as printed. mode = 0 and forms A, B, C
  * give exactly the outputs of prng_fill_f64 / prng_fill_f32pair. The streams advance as the
  * reject rule consumes draws. d_out: device memory, 8-byte aligned; the fast (TMA) path needs

@@ -9,7 +9,7 @@ from . import build as _build
 
 PRNG_OK, PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA, PRNG_ETIMEOUT, PRNG_EBUSY, PRNG_ENOTFOUND = range(7)
 FORM_A_FP64, FORM_B_INTBITS, FORM_C_F32PAIR, FORM_L_ALGO1 = 0, 1, 2, 4
-MODE_EQ5, MODE_ONE_MINUS, MODE_SINGLE_REDRAW, MODE_FP64_ROUND = 1, 2, 4, 8
+MODE_EQ5, MODE_ONE_MINUS, MODE_SINGLE_REDRAW, MODE_BALANCED = 1, 2, 4, 8
 GEN_XORSHIFT128, GEN_MRG32K3A = 0, 1
 REQ_FRESH, REQ_RESIDENT = 0, 1
 MAX_BATCH_REQUESTS = 4096

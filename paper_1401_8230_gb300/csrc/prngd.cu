@@ -143,12 +143,12 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kNbuf = 1;  // one tile per warp: 4 blocks of 8 warps fit per SM (registers and shared memory)
 constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * kNbuf * prngd::kTileBytes + 1024;
 
-template <int W, int FORM>
+template <int W, int FORM, int MAP = 0>
 static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s) {
   const uint64_t warps = (p.n_streams + 31) / 32;
   const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (map) {
-    auto k = prngd::fill_tma_kernel<W, FORM, kNbuf>;
+    auto k = prngd::fill_tma_kernel<W, FORM, kNbuf, MAP>;
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
@@ -157,16 +157,16 @@ static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cu
     }
     k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
   } else {
-    prngd::fill_plain_kernel<W, FORM><<<blocks, kWarpsPerBlock * 32, 0, s>>>(p);
+    prngd::fill_plain_kernel<W, FORM, MAP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(p);
   }
   return cudaGetLastError();
 }
 
-template <int FORM>
+template <int FORM, int MAP = 0>
 static cudaError_t launch_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s) {
-  if (p.w == 32) return launch_w_form<32, FORM>(p, map, s);
-  if (p.w == 24) return launch_w_form<24, FORM>(p, map, s);
-  return launch_w_form<0, FORM>(p, map, s);
+  if (p.w == 32) return launch_w_form<32, FORM, MAP>(p, map, s);
+  if (p.w == 24) return launch_w_form<24, FORM, MAP>(p, map, s);
+  return launch_w_form<0, FORM, MAP>(p, map, s);
 }
 
 // Host memory the device can address (pinned / registered); its device-side address in *dev.
@@ -212,7 +212,12 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
   const bool fast = mp && (h->w == 32 || h->w == 24) &&
                     (form == PRNG_FORM_B_INTBITS || form == PRNG_FORM_C_F32PAIR);
   int map_bits = map_bits_of(form, mode);
-  if (!fast) map_bits &= ~prngd::kMapCvt;
+  if (!fast && form != PRNG_FORM_A_FP64) map_bits &= ~prngd::kMapCvt;  // form B's route: pair kernels only
+  if (form == PRNG_FORM_A_FP64 && map_bits == prngd::kMapCvt) {  // balanced form A under Eq. 4
+    e = launch_form<prngd::kFormA, prngd::kMapCvt>(p, mp, s);
+    if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));
+    return PRNG_OK;
+  }
   if (map_bits || form == PRNG_FORM_L_ALGO1) {
     e = fast ? launch_fill_map_fast(p, form, map_bits, mp, s) : launch_fill_map(p, form, map_bits, mp, s);
     if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));

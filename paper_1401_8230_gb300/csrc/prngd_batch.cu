@@ -112,7 +112,7 @@ static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape&
                                   cudaStream_t s) {
   switch (form_all) {
     case prngd::kAnyMode: return launch_batch_any_mode_w<W>(p, sh, num_sms, s);
-    case prngd::kFormBRound: return launch_batch_wf<W, prngd::kFormBRound>(p, sh, num_sms, s);
+    case prngd::kFormBBalanced: return launch_batch_wf<W, prngd::kFormBBalanced>(p, sh, num_sms, s);
     case prngd::kFormA: return launch_batch_wf<W, prngd::kFormA>(p, sh, num_sms, s);
     case prngd::kFormB: return launch_batch_wf<W, prngd::kFormB>(p, sh, num_sms, s);
     case prngd::kFormC: return launch_batch_wf<W, prngd::kFormC>(p, sh, num_sms, s);
@@ -268,18 +268,18 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
     prngd::BatchDesc& q = sl->h_desc[i];
     if (q.full_rows < 32 || !encode_out_map(&sl->h_maps[i], q.out, q.full_rows, q.per_stream)) q.full_rows = 0;
   }
-  // kernel: one form, mode 0 -> a single-form kernel; form B with exactly PRNG_MODE_FP64_ROUND
+  // kernel: one form, mode 0 -> a single-form kernel; form B with exactly PRNG_MODE_BALANCED
   // -> its single-form kernel; forms A, B, C, mode 0 -> the mixed-form kernel; otherwise the
   // any-mode kernel
   int form_all = d[0].form;
   for (int i = 1; i < n && form_all >= 0; ++i)
     if (d[i].form != form_all) form_all = -1;
-  bool all_b_round = true;  // every request form B with exactly PRNG_MODE_FP64_ROUND
+  bool all_b_round = true;  // every request form B with exactly PRNG_MODE_BALANCED
   for (int i = 0; i < n; ++i)
-    all_b_round = all_b_round && d[i].form == PRNG_FORM_B_INTBITS && d[i].mode == PRNG_MODE_FP64_ROUND;
+    all_b_round = all_b_round && d[i].form == PRNG_FORM_B_INTBITS && d[i].mode == PRNG_MODE_BALANCED;
   for (int i = 0; i < n; ++i)
     if (d[i].mode || d[i].form == PRNG_FORM_L_ALGO1) form_all = prngd::kAnyMode;
-  if (all_b_round) form_all = prngd::kFormBRound;
+  if (all_b_round) form_all = prngd::kFormBBalanced;
   rc = ensure_graph(h, *sl, form_all);
   if (rc) return rc;
   cudaError_t e = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(prngd::BatchDesc) * n, cudaMemcpyHostToDevice, s);

@@ -15,7 +15,7 @@
 namespace prngd {
 
 constexpr uint32_t kModeSingle = 4;      // BatchDesc::mode bit: Algorithm 1's single-redraw rejects
-constexpr uint32_t kModeFp64Round = 8;   // BatchDesc::mode bit: form B's FP64 rounding route
+constexpr uint32_t kModeBalanced = 8;    // BatchDesc::mode bit: PRNG_MODE_BALANCED (forms A and B)
 
 struct BatchDesc {       // 64 bytes, built on the host
   uint64_t seed;         // fresh: seed of the streams
@@ -273,8 +273,8 @@ __device__ __noinline__ void batch_item_fm(const BatchDesc* __restrict__ dp, con
 template <int W, int FORM>
 __device__ __forceinline__ void batch_item_form_any_map(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
                                                         uint64_t row0, const BatchParams& bp, uint32_t tile, int lane) {
-  if constexpr (FORM == kFormB) {
-    if (dp->mode & kModeFp64Round) {
+  if constexpr (FORM == kFormB || FORM == kFormA) {  // the balanced routes
+    if (dp->mode & kModeBalanced) {
       switch (dp->mode & (kMapEq5 | kMapOneMinus)) {
         case 0: batch_item_fm<W, FORM, kMapCvt>(dp, map, row0, bp, tile, lane); break;
         case kMapEq5: batch_item_fm<W, FORM, kMapCvt | kMapEq5>(dp, map, row0, bp, tile, lane); break;
@@ -301,9 +301,9 @@ __device__ __forceinline__ void batch_item_form_any_map(const BatchDesc* __restr
 // In the first two the reject rule is fixed at compile time, so the hot loop carries the code
 // of one rule only.
 constexpr int kAnyMode = -2;
-// kFormBRound: every request is form B with exactly PRNG_MODE_FP64_ROUND (form B's values with
+// kFormBBalanced: every request is form B with exactly PRNG_MODE_BALANCED (form B's values with
 // 3 of 4 outputs rounded on the FP64 pipe), in a single-form kernel like FORM_ALL = kFormB.
-constexpr int kFormBRound = 3;
+constexpr int kFormBBalanced = 3;
 
 // The mixed-form kernel gives its FP64 pipe to form A's conversion and rounds forms B and C with
 // integer operations. Measured on the batch of forms A/B/C interleaved (Gsamples/s): this 630;
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
           case kFormL: batch_item_form_any_map<W, kFormL>(dp, bp.maps + r, row0, bp, tile, lane); break;
           default: batch_item_form_any_map<W, kFormB>(dp, bp.maps + r, row0, bp, tile, lane); break;
         }
-      } else if constexpr (FORM_ALL == kFormBRound) {
+      } else if constexpr (FORM_ALL == kFormBBalanced) {
         batch_item<W, kFormB, kMapCvt>(dp, bp.maps + r, row0, bp, fp, tile, lane);
       } else if constexpr (FORM_ALL >= 0) {
         batch_item<W, FORM_ALL>(dp, bp.maps + r, row0, bp, fp, tile, lane);

@@ -40,7 +40,7 @@ template <int W, int FORM>
 cudaError_t by_map(int map, const prngd::FillParams& p, const uint32_t* u1, const uint32_t* u2, uint64_t n,
                    uint64_t* out, cudaStream_t s) {
   constexpr int E = prngd::kMapEq5, O = prngd::kMapOneMinus, V = prngd::kMapCvt;
-  if constexpr (FORM == prngd::kFormB) {  // form B's FP64 rounding route
+  if constexpr (FORM == prngd::kFormB || FORM == prngd::kFormA) {  // the balanced routes
     switch (map) {
       case V: return launch_convert<W, FORM, V>(p, u1, u2, n, out, s);
       case V | E: return launch_convert<W, FORM, V | E>(p, u1, u2, n, out, s);

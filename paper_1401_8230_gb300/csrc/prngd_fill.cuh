@@ -14,17 +14,18 @@ constexpr int kChunk = 16;         // outputs per stream per staged tile (128 by
 constexpr int kTileBytes = 32 * kChunk * 8;  // one warp: 32 streams x 16 outputs x 8 bytes
 
 enum Form : int { kFormA = 0, kFormB = 1, kFormC = 2, kFormL = 4, kFormAF = 8 };
-// kFormAF: form A's outputs, with RN(n) taken by the conversion instruction (FP64 pipe) instead of
-// integer rounding (ALU pipe). Alone, form A is faster with the integer rounding, since FP64
-// issue is scarce; beside the ALU-bound forms B and C in one kernel, the FP64 pipe is idle and
-// the conversion overlaps with their integer work.
+// Form A takes RN(n) by the u64 -> f64 conversion instruction (its definition: the conversion
+// and the final scale are its FP64 steps) unless MAP has kMapCvt (PRNG_MODE_BALANCED): then by
+// integer rounding, the same bits with the ALU pipe's help, since FP64 issue is scarce.
+// kFormAF forces the conversion instruction under either MAP.
 
 // Map bits (template parameter MAP of the per-output code): the map of Eq. 5 (one generator:
 // Eq. 6) instead of Eq. 4, and 1 - z instead of z. MAP = 0 is Eq. 4.
 constexpr int kMapEq5 = 1;
 constexpr int kMapOneMinus = 2;
-// Not a map: form B's rounding may use the FP64 conversion (PRNG_MODE_FP64_ROUND); the values
-// are the same, so only cvt_group_mask reads this bit.
+// Not a map: PRNG_MODE_BALANCED, the same values by a route that shares the work between the
+// integer and FP64 pipes (form B: 3 of 4 outputs rounded by the FP64 conversion, see
+// cvt_group_mask; form A: n converted with integer operations).
 constexpr int kMapCvt = 4;
 
 struct FillParams {
@@ -106,15 +107,16 @@ __device__ __forceinline__ uint64_t convert_exact(uint32_t u1, uint32_t u2, cons
   if constexpr (FORM == kFormL) {
     return form_l_bits<MAP>(u1, u2, p);
   } else if constexpr (FORM == kFormA || FORM == kFormAF) {
+    constexpr bool kIntRound = FORM == kFormA && (MAP & kMapCvt) != 0;
     double z;
     if constexpr ((MAP & kMapEq5) != 0) {
       const uint64_t m = ((uint64_t)(u1 - 1u) << w) + u2;  // 0 for the pair mapped to z' = 0
-      const double rm = (FORM == kFormAF) ? __ull2double_rn(m)
-                                          : __longlong_as_double((long long)(m ? u64_to_f64_bits(m) : 0ull));
+      const double rm = kIntRound ? __longlong_as_double((long long)(m ? u64_to_f64_bits(m) : 0ull))
+                                  : __ull2double_rn(m);
       z = __dmul_rn(rm, p.scale5);  // RN(RN(m) C5)
     } else {
       const uint64_t n = numerator(u1, u2, w);
-      const double rn = (FORM == kFormAF) ? __ull2double_rn(n) : __longlong_as_double((long long)u64_to_f64_bits(n));
+      const double rn = kIntRound ? __longlong_as_double((long long)u64_to_f64_bits(n)) : __ull2double_rn(n);
       z = __dmul_rn(rn, p.scale);  // RN(RN(n) C_w)
     }
     if constexpr ((MAP & kMapOneMinus) != 0) z = __dsub_rn(1.0, z);
@@ -351,7 +353,7 @@ __device__ __forceinline__ uint32_t fast32_I_pair(uint32_t x, uint32_t y, uint32
 // (form C spends more ALU work per output on the float pair, so the FP64 pipe has room for all).
 template <int FORM, int W = 32, int MAP = 0>
 __device__ __forceinline__ constexpr uint32_t cvt_group_mask() {
-  return FORM == kFormC ? 0xFu : ((MAP & kMapCvt) ? 0xEu : 0x0u);
+  return FORM == kFormC ? 0xFu : ((FORM == kFormB && (MAP & kMapCvt)) ? 0xEu : 0x0u);
 }
 
 // The w = 24 fast path of fast24_ok / fast24_bits as PTX, from the raw 32-bit words (the draws
@@ -646,10 +648,11 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
         for (int j = 0; j < kChunk; j += 2)
           next_pair<W, FORM, MAP>(st, rej, p, v[j], v[j + 1], (cvt_group_mask<FORM, W, MAP>() >> (j & 3)) & 1u,
                                   (cvt_group_mask<FORM, W, MAP>() >> ((j + 1) & 3)) & 1u);
-      } else if constexpr (FORM == kFormA && W == 32) {
-        // one output in eight converts on the FP64 pipe (kFormAF), which the integer rounding
-        // leaves idle: measured 446 against 425 Gsamples/s for none (one in two: 352, in four:
-        // 401). Not at w = 24, where n < 2^53 converts exactly and cheaply (517 against 460).
+      } else if constexpr (FORM == kFormA && W == 32 && (MAP & kMapCvt) != 0) {
+        // balanced form A: one output in eight still converts on the FP64 pipe (kFormAF), which
+        // the integer rounding leaves idle: measured 446 against 425 Gsamples/s for none (one in
+        // two: 352, in four: 401). Not at w = 24, where n < 2^53 converts exactly and cheaply
+        // (517 against 460).
 #pragma unroll
         for (int j = 0; j < kChunk; ++j)
           v[j] = (j % 8 == 0) ? next_output<W, kFormAF, MAP>(st, rej, p) : next_output<W, FORM, MAP>(st, rej, p);

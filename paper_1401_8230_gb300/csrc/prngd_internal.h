@@ -53,14 +53,14 @@ int check_handle_device(prng_ctx* h);
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                 uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode = 0);
 // Every PRNG_MODE_* bit an entry point accepts.
-constexpr int kAllModes = PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW | PRNG_MODE_FP64_ROUND;
-// The kernels' MAP bits of a mode: the map bits (mode & 3), and for form B the conversion
-// route of PRNG_MODE_FP64_ROUND (kMapCvt = 4 in prngd_fill.cuh).
+constexpr int kAllModes = PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS | PRNG_MODE_SINGLE_REDRAW | PRNG_MODE_BALANCED;
+// The kernels' MAP bits of a mode: the map bits (mode & 3), and for forms A and B the balanced
+// route of PRNG_MODE_BALANCED (kMapCvt = 4 in prngd_fill.cuh).
 inline int map_bits_of(int form, int mode) {
   return (mode & (PRNG_MODE_EQ5 | PRNG_MODE_ONE_MINUS)) |
-         ((form == PRNG_FORM_B_INTBITS && (mode & PRNG_MODE_FP64_ROUND)) ? 4 : 0);
+         (((form == PRNG_FORM_B_INTBITS || form == PRNG_FORM_A_FP64) && (mode & PRNG_MODE_BALANCED)) ? 4 : 0);
 }
-// Kernels for the Eq. 5 / 1 - z maps, the FP64 rounding route and form L (prngd_modes.cu,
+// Kernels for the Eq. 5 / 1 - z maps, the balanced routes and form L (prngd_modes.cu,
 // prngd_modes_fast.cu): `map` as map_bits_of; `tmap` is null for the plain store path.
 cudaError_t launch_fill_map(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap, cudaStream_t s);
 cudaError_t launch_fill_map_fast(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap,

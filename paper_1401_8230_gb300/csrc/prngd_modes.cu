@@ -34,7 +34,17 @@ cudaError_t launch_generic(const prngd::FillParams& p, const CUtensorMap* tmap, 
 
 template <int FORM>
 cudaError_t launch_form_map(const prngd::FillParams& p, int map, const CUtensorMap* tmap, cudaStream_t s) {
-  switch (map & ~prngd::kMapCvt) {  // the generic code has no conversion route
+  if constexpr (FORM == prngd::kFormA) {  // balanced form A (integer conversion) under a map
+    constexpr int E = prngd::kMapEq5, O = prngd::kMapOneMinus, V = prngd::kMapCvt;
+    switch (map) {
+      case V: return launch_generic<FORM, V>(p, tmap, s);
+      case V | E: return launch_generic<FORM, V | E>(p, tmap, s);
+      case V | O: return launch_generic<FORM, V | O>(p, tmap, s);
+      case V | E | O: return launch_generic<FORM, V | E | O>(p, tmap, s);
+      default: break;
+    }
+  }
+  switch (map & ~prngd::kMapCvt) {  // form B's rounding route exists in the pair kernels only
     case 0: return launch_generic<FORM, 0>(p, tmap, s);
     case prngd::kMapEq5: return launch_generic<FORM, prngd::kMapEq5>(p, tmap, s);
     case prngd::kMapOneMinus: return launch_generic<FORM, prngd::kMapOneMinus>(p, tmap, s);

@@ -1,5 +1,5 @@
 // prngd_modes_fast.cu -- fill kernels for the Eq. 5 and 1 - z maps (Section 2) at w = 32 and
-// w = 24, forms B and C, and form B's FP64 rounding route: the pair fast paths of
+// w = 24, forms B and C, and form B's balanced route: the pair fast paths of
 // prngd_fill.cuh with the map as a template parameter, TMA tile stores. Separate from prngd.cu so the instantiations compile in parallel.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -36,7 +36,7 @@ cudaError_t launch_map(const prngd::FillParams& p, int map, const CUtensorMap* t
     case E | O: return launch_fast<W, FORM, E | O>(p, tmap, s);
     default: break;
   }
-  if constexpr (FORM == prngd::kFormB) {  // form B's FP64 rounding route
+  if constexpr (FORM == prngd::kFormB) {  // form B's balanced route
     switch (map) {
       case V: return launch_fast<W, FORM, V>(p, tmap, s);
       case V | E: return launch_fast<W, FORM, V | E>(p, tmap, s);

@@ -58,7 +58,8 @@ __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, 
     ++rej;
   }
   const uint64_t n = (uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u);
-  if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__longlong_as_double((long long)u64_to_f64_bits(n)), p.scale));
+  // form A: the conversion instruction, then the scale (its definition's two FP64 steps)
+  if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
   const uint64_t bits = rn_bits_exact(n, p.dc);
   return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }
@@ -160,8 +161,8 @@ cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, 
 int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                     uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode) {
   if (n_streams == 0 || per_stream == 0) return PRNG_OK;
-  // PRNG_MODE_FP64_ROUND changes no value, and the MRG conversion has no such route: ignored
-  if ((mode & ~PRNG_MODE_FP64_ROUND) != 0 ||
+  // PRNG_MODE_BALANCED changes no value, and the MRG conversion has no such route: ignored
+  if ((mode & ~PRNG_MODE_BALANCED) != 0 ||
       (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR))
     return fail(PRNG_EINVAL, "MRG32k3a streams take forms A, B and C with mode 0");
   if (allow_tma && device_mapped_host(out, nullptr)) allow_tma = false;

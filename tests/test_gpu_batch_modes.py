@@ -4,7 +4,7 @@ Eq. (5)/(6) map, 1 - z, Algorithm 1's single-redraw rejects) and form L (Algorit
 A request's mode changes only what each of its rows computes: the rows are the oracle's fill
 of the same streams with the same mode. Batches mix modes and forms, so every kernel the batch
 path selects is exercised: one form in mode 0 (single-form kernel), form B with
-PRNG_MODE_FP64_ROUND alone (its single-form kernel), forms A/B/C in mode 0 (mixed-form kernel),
+PRNG_MODE_BALANCED alone (its single-form kernel), forms A/B/C in mode 0 (mixed-form kernel),
 and any form and mode (any-mode kernel); full 32-row items
 (tensor-map stores) and ragged ones, at w = 32, 24 and a small w where rejects are frequent."""
 import numpy as np
@@ -102,19 +102,19 @@ def test_any_mode_batch_matches_the_oracle(w):
             mode = m | (P.MODE_SINGLE_REDRAW if (i + j) % 2 else 0)
             cases.append((L, chunk, form, mode))
     cases.append((64 * 70 + 13, 64, P.FORM_B_INTBITS, P.MODE_EQ5))
-    F = P.MODE_FP64_ROUND  # form B's FP64 rounding route: the oracle's values without the bit
+    F = P.MODE_BALANCED  # the balanced routes of forms A and B: the oracle's values without the bit
     cases += [(64 * 70 + 13, 64, P.FORM_B_INTBITS, F), (1025, 0, P.FORM_B_INTBITS, F | P.MODE_EQ5),
               (40 * 48, 48, P.FORM_B_INTBITS, F | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW),
-              (999, 2, P.FORM_C_F32PAIR, F)]
+              (999, 2, P.FORM_C_F32PAIR, F), (1025, 0, P.FORM_A_FP64, F), (64 * 70 + 13, 64, P.FORM_A_FP64, F | P.MODE_EQ5)]
     with P.Generator(3, 1, w) as g:
         run_fresh_batch(g, cases, w)
 
 
 @pytest.mark.parametrize("w", [32, 24, 5])
-def test_fp64_rounding_batches(w):
-    """Batches whose requests are all form B with PRNG_MODE_FP64_ROUND (their own single-form
+def test_balanced_batches(w):
+    """Batches whose requests are all form B with PRNG_MODE_BALANCED (their own single-form
     kernel): fresh requests of every shape and resident requests give the oracle's form B."""
-    F = P.MODE_FP64_ROUND
+    F = P.MODE_BALANCED
     with P.Generator(6, 1, w) as g:
         run_fresh_batch(g, [(L, c, P.FORM_B_INTBITS, F) for L, c in SHAPES * 2], w)
     seed, ns = 9, 96

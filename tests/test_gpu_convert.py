@@ -18,7 +18,7 @@ import paper_1401_8230_gb300 as P  # noqa: E402
 OF = {P.FORM_A_FP64: O.FORM_A, P.FORM_B_INTBITS: O.FORM_B, P.FORM_C_F32PAIR: O.FORM_C, P.FORM_L_ALGO1: O.FORM_L}
 OM = {0: 0, P.MODE_EQ5: O.MODE_EQ5, P.MODE_ONE_MINUS: O.MODE_ONE_MINUS,
       P.MODE_EQ5 | P.MODE_ONE_MINUS: O.MODE_EQ5 | O.MODE_ONE_MINUS}
-F = P.MODE_FP64_ROUND  # form B's FP64 rounding route: the same values
+F = P.MODE_BALANCED  # the balanced routes of forms A and B: the same values
 OM.update({F | k: v for k, v in list(OM.items())})
 
 

@@ -42,9 +42,9 @@ def same(a, b):
     return np.array_equal(np.ascontiguousarray(a).view(np.uint8), np.ascontiguousarray(b).view(np.uint8))
 
 
-# PRNG_MODE_FP64_ROUND changes no value (form B's rounding route only), so the oracle has no bit
-# for it: every case with it must equal the oracle's output without it.
-F = P.MODE_FP64_ROUND
+# PRNG_MODE_BALANCED changes no value (forms A and B take another route to the same bits), so
+# the oracle has no bit for it: every case with it must equal the oracle's output without it.
+F = P.MODE_BALANCED
 MODES = [P.MODE_EQ5, P.MODE_ONE_MINUS, P.MODE_EQ5 | P.MODE_ONE_MINUS, P.MODE_SINGLE_REDRAW,
          P.MODE_EQ5 | P.MODE_SINGLE_REDRAW, P.MODE_EQ5 | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW,
          F, F | P.MODE_EQ5, F | P.MODE_ONE_MINUS, F | P.MODE_EQ5 | P.MODE_ONE_MINUS | P.MODE_SINGLE_REDRAW]
@@ -115,9 +115,10 @@ def test_mode_zero_is_the_plain_fill():
 
 
 @pytest.mark.parametrize("w", [32, 24, 17])
-def test_fp64_rounding_route_gives_form_b(w):
-    """Form B with PRNG_MODE_FP64_ROUND equals integer-only form B bit for bit (TMA and plain
-    stores; w = 17 has no such route and must ignore the bit); other forms ignore it."""
+def test_balanced_route_gives_the_same_values(w):
+    """PRNG_MODE_BALANCED changes no value: form B (3 of 4 outputs rounded on the FP64 pipe),
+    form A (n converted with integer operations) and form C equal their mode-0 fills bit for bit,
+    with TMA and plain stores, at w = 32, 24 and 17."""
     for per, offset in [(1024, 0), (333, 0), (64, 1)]:
         for form in (P.FORM_B_INTBITS, P.FORM_C_F32PAIR, P.FORM_A_FP64):
             with P.Generator(13, 256, w) as a, P.Generator(13, 256, w) as b:

@@ -85,7 +85,7 @@ def test_split_equals_plain_fill(w, segments):
 @pytest.mark.parametrize("form,mode", [(P.FORM_A_FP64, 0), (P.FORM_C_F32PAIR, 0), (P.FORM_L_ALGO1, 0),
                                        (P.FORM_B_INTBITS, P.MODE_EQ5), (P.FORM_B_INTBITS, P.MODE_ONE_MINUS),
                                        (P.FORM_C_F32PAIR, P.MODE_EQ5 | P.MODE_ONE_MINUS),
-                                       (P.FORM_B_INTBITS, P.MODE_FP64_ROUND)])
+                                       (P.FORM_B_INTBITS, P.MODE_BALANCED)])
 @pytest.mark.parametrize("w", [4, 24])
 def test_split_forms_and_maps(form, mode, w):
     seed, ns, per = 6, 12, 2048
