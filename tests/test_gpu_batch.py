@@ -209,3 +209,33 @@ def test_batched_workload_sampled():
             got = pool[offs[i]:offs[i] + r["length"]].cpu().numpy()
             want, _ = oracle_fresh(r["seed"], r["first_stream"], r["length"], 1024, 32, P.FORM_B_INTBITS)
             assert same(got, want), i
+
+
+def test_bounded_waits_report_timeouts_and_recover():
+    """The host-side waits are bounded: prng_wait and prng_server_drain with a zero timeout on
+    work still running answer PRNG_ETIMEOUT (no kernel waits on anything; nothing can hang), and
+    the same handle then finishes and gives the oracle's values."""
+    L = 2**30  # ~1.5 ms of device work: still running when the first poll comes back
+    with P.Generator(1, 1, 32) as g:
+        big = torch.empty(L, dtype=torch.float64, device="cuda")
+        t = P.prng_submit(g.h, [P.fresh_request(big, L, 12, 0)])
+        with pytest.raises(P.PrngError) as e:
+            P.prng_wait(g.h, t, 0.0)
+        assert e.value.code == P.PRNG_ETIMEOUT
+        P.prng_wait(g.h, t, 60)
+        got = big[1024 * 777:1024 * 778].cpu().numpy()
+        want, _ = O.fill(12, 777, 1, 1024, 32, O.FORM_B)
+        assert same(got, want)
+        del big
+        torch.cuda.empty_cache()
+    with P.Generator(2, 4 * 4096, 32) as g:
+        srv = P.prng_server_create(g.h, 4096, 1024, 8 << 30)
+        try:
+            ids = [P.prng_server_submit(srv, c, 2**28, P.FORM_B_INTBITS) for c in range(4)]
+            with pytest.raises(P.PrngError) as e:
+                P.prng_server_drain(srv, 0.0)
+            assert e.value.code == P.PRNG_ETIMEOUT
+            P.prng_server_drain(srv, 60)
+            assert all(P.prng_server_poll(srv, i)[0] for i in ids)
+        finally:
+            P.prng_server_destroy(srv)
