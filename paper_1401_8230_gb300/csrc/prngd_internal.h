@@ -45,6 +45,7 @@ struct prng_ctx {
   size_t split_bytes = 0;
   uint64_t split_table_seg = 0;     // segment length the jump table in the scratch was built for
   void* split_table_mem = nullptr;  // where that table lives
+  int split_table_digits = 0;       // digits of the segment index it covers
 };
 
 namespace prngd_host {

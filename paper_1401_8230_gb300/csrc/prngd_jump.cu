@@ -29,16 +29,20 @@
 namespace prngd {
 
 constexpr int kMaxSplitLog2 = 23;  // at most 2^23 segments per stream
-constexpr int kJumpDigits = 3;      // segment index in base 256: at most 3 jumps per segment
+// Segment index in base 8192: one jump for up to 8192 segments per stream, two beyond (the
+// table holds 128 KiB per digit; base 256 took two jumps at 8192 segments, 8% of a split fill).
+constexpr int kJumpDigitBits = 13;
+constexpr uint32_t kJumpBase = 1u << kJumpDigitBits;
+constexpr int kJumpDigits = 2;  // 26 bits >= kMaxSplitLog2
 
-// T^(delta j) s from a table of jump polynomials over the base-256 digits of j:
-// table[d * 256 + k] = x^(delta k 256^d) mod P (k = 0 entries unused).
+// T^(delta j) s from a table of jump polynomials over the base-8192 digits of j:
+// table[d * 8192 + k] = x^(delta k 8192^d) mod P (k = 0 entries unused).
 __device__ __forceinline__ XorShift128 jump_to_segment(const uint4* __restrict__ table, uint32_t j, XorShift128 st) {
 #pragma unroll 1
   for (int d = 0; d < kJumpDigits; ++d) {
-    const uint32_t k = (j >> (8 * d)) & 255u;
+    const uint32_t k = (j >> (kJumpDigitBits * d)) & (kJumpBase - 1u);
     if (k) {
-      const uint4 q = table[d * 256 + k];
+      const uint4 q = table[d * kJumpBase + k];
       const uint32_t g[4] = {q.x, q.y, q.z, q.w};
       st = apply_poly(g, st);
     }
@@ -81,7 +85,7 @@ struct SplitArgs {
   uint64_t n_streams;
   uint32_t log2s;
   uint64_t seg;          // attempts (outputs) per segment
-  const uint4* table;    // jump polynomials over the base-256 digits of the segment index
+  const uint4* table;    // jump polynomials over the base-8192 digits of the segment index
 };
 
 // Per segment row: a row whose main pass met a reject lowers its stream's first-bad marker.
@@ -241,6 +245,7 @@ void release_split(prng_ctx* h) {
   h->split_bytes = 0;
   h->split_table_seg = 0;
   h->split_table_mem = nullptr;
+  h->split_table_digits = 0;
 }
 
 int skip_streams(prng_ctx* h, uint64_t draws, cudaStream_t s) {
@@ -284,7 +289,7 @@ int fill_split(prng_ctx* h, void* out, uint64_t per_stream, int form, int mode, 
   // scratch: the jump table first (a fixed place, so a later call never overwrites it), then per
   // row the state (16 B), the main-pass rejects (8 B) and the nominal rejects (4 B), then per
   // stream the tail state (16 B), the first bad segment and the total (4 B each)
-  const size_t table_bytes = prngd::kJumpDigits * 256 * 16;
+  const size_t table_bytes = (size_t)prngd::kJumpDigits * prngd::kJumpBase * 16;
   const size_t bytes = table_bytes + n_rows * 28 + h->n_streams * 24 + 256;
   if (h->split_bytes < bytes) {
     release_split(h);
@@ -317,27 +322,30 @@ int fill_split(prng_ctx* h, void* out, uint64_t per_stream, int form, int mode, 
   a.log2s = (uint32_t)log2s;
   a.seg = seg;
   a.table = table;
-  if (h->split_table_seg != seg || h->split_table_mem != (void*)table) {
-    // x^(delta k 256^d) mod P for d < 3, k < 256, delta = 2 seg draws (pair rule); built on the
-    // host once per segment length and copied next to the scratch
+  const int digits = (log2s + prngd::kJumpDigitBits - 1) / prngd::kJumpDigitBits;  // digits j can have
+  if (h->split_table_seg != seg || h->split_table_mem != (void*)table || h->split_table_digits < digits) {
+    // x^(delta k 8192^d) mod P for the digits segment indices use, k < 8192, delta = 2 seg draws
+    // (pair rule); built on the host once per segment length (a few ms a digit) and copied to
+    // the start of the scratch
     static thread_local std::vector<uint4> host;
-    host.assign(prngd::kJumpDigits * 256, make_uint4(0, 0, 0, 0));
+    host.assign((size_t)digits * prngd::kJumpBase, make_uint4(0, 0, 0, 0));
     Poly step = x_pow(2 * seg);
-    for (int d = 0; d < prngd::kJumpDigits; ++d) {
+    for (int d = 0; d < digits; ++d) {
       Poly acc{1, 0};
-      for (int k = 1; k < 256; ++k) {
+      for (uint32_t k = 1; k < prngd::kJumpBase; ++k) {
         acc = mulmod(acc, step);
         uint32_t g[4];
         words_of(acc, g);
-        host[d * 256 + k] = make_uint4(g[0], g[1], g[2], g[3]);
+        host[(size_t)d * prngd::kJumpBase + k] = make_uint4(g[0], g[1], g[2], g[3]);
       }
-      step = mulmod(acc, step);  // x^(delta 256^(d+1))
+      step = mulmod(acc, step);  // x^(delta 8192^(d+1))
     }
     cudaError_t ce = cudaMemcpyAsync(table, host.data(), host.size() * sizeof(uint4), cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // `host` is reused by the next call
     if (ce != cudaSuccess) return fail(PRNG_ECUDA, "jump table copy: %s", cudaGetErrorString(ce));
     h->split_table_seg = seg;
     h->split_table_mem = table;
+    h->split_table_digits = digits;
   }
   const unsigned rb = (unsigned)((n_rows + 255) / 256);
   prngd::jump_rows_kernel<<<rb, 256, 0, s>>>(h->d_state, rows, n_rows, log2s, table, first_bad);
