@@ -405,7 +405,12 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
     fn()
     ms = sum(time_calls(torch, fn, reps, stream)) / reps
     res["mrg32k3a_formB"] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak,
-                             "note": "2^20 MRG32k3a streams x 1024, M = m1 grid, exact division"}
+                             "note": "2^20 MRG32k3a streams x 1024, M = m1 grid, series fast path"}
+    fn = lambda: gm.fill_mode(out, PER_STREAM, P.FORM_B_INTBITS, P.MODE_BALANCED, None, stream)  # noqa: E731
+    fn()
+    ms = sum(time_calls(torch, fn, reps, stream)) / reps
+    res["mrg32k3a_formB_balanced"] = {"gsamples_s": rate(ms), "ms": ms,
+                                      "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak}
     gm.close()
     g24 = P.Generator(SEED, N_STREAMS, 24)
     for name, form, mode in [("w24_formB_intbits", P.FORM_B_INTBITS, 0),

@@ -100,7 +100,8 @@ int prng_create(prng_t* out, uint64_t seed, uint64_t n_streams, int w, double a0
  * n = u1 M + u2 - (M - 1), D = (M - 1)^2. Stream s is seeded from splitmix64 outputs 3s, 3s+1
  * and 3s+2 of `seed` (six 32-bit words, low first, reduced modulo m1 and m2; an all-zero
  * component gets 1 as its first word). 32 bytes of device state per stream.
- * Such a handle takes prng_fill_f64, prng_fill_f32pair, prng_fill_mode (mode 0, forms A, B, C),
+ * Such a handle takes prng_fill_f64, prng_fill_f32pair, prng_fill_mode (forms A, B, C; mode 0 or
+ * PRNG_MODE_BALANCED),
  * prng_fill_f64_host(_noalloc) and prng_state_*; the entry points built on xorshift128's
  * structure (fused statistics, batches, serving, skip, split) answer PRNG_EINVAL.
  * Errors: PRNG_EINVAL (out == NULL, n_streams == 0 or > 2^32), PRNG_ENOMEM, PRNG_ECUDA.

@@ -6,7 +6,8 @@
 // combined as z = (x1 - x2) mod m1 in [1, m1] (0 reported as m1). The method reads z as the
 // draw u = z - 1 on a grid of M = m1 points with step k = 1/M, so Section 2 holds with 2^w
 // replaced by M: pairs with u1 in {0, M - 1} are rejected and z' = n / D with
-// n = u1 M + u2 - (M - 1), D = (M - 1)^2 < 2^64, converted exactly (Moller-Granlund division).
+// n = u1 M + u2 - (M - 1), D = (M - 1)^2 < 2^64, converted by a series fast path (mrg_fast_I)
+// or exactly (Moller-Granlund division) for small values and margin cases.
 //
 // State: 32 bytes per stream in the handle's state array (two uint4: x1_{n-3}, x1_{n-2},
 // x1_{n-1}, x2_{n-3} | x2_{n-2}, x2_{n-1}, 0, 0), seeded from splitmix64 outputs 3s, 3s+1, 3s+2.
@@ -47,8 +48,9 @@ __global__ void mrg_seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
   mrg_store(state, s, g);
 }
 
-// One output of the method over MRG32k3a draws (pair rule), 8 bytes of form FORM.
-template <int FORM>
+// One output of the method over MRG32k3a draws (pair rule), 8 bytes of form FORM; MAP is 0 or
+// kMapCvt (PRNG_MODE_BALANCED, form B's rounding route).
+template <int FORM, int MAP = 0>
 __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, const FillParams& p) {
   uint32_t u1, u2;
   for (;;) {
@@ -60,13 +62,22 @@ __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, 
   const uint64_t n = (uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u);
   // form A: the conversion instruction, then the scale (its definition's two FP64 steps)
   if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
-  const uint64_t bits = rn_bits_exact(n, p.dc);
+  uint64_t bits;
+  uint32_t ok = 0;
+  if (__builtin_expect(u1 > (1u << 22), 1)) {  // A >= 2^22: the series fast path
+    const uint64_t I = mrg_fast_I(n, ok);
+    // the fills' rounding routes (cvt_group_mask): form C by the conversion instruction; form B
+    // by integer operations, or by the conversion under PRNG_MODE_BALANCED (measured 182 and
+    // 187 Gsamples/s; form C 174)
+    bits = cvt_group_mask<FORM, 32, MAP>() ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
+  }
+  if (__builtin_expect(!ok, 0)) bits = rn_bits_exact(n, p.dc);  // small values, margin cases
   return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }
 
 // Tile-staged TMA path, as the xorshift fill kernel: warp g owns streams 32g .. 32g+31, 16
 // outputs per lane per chunk through a 128-byte-swizzled tile and one 2D tensor store.
-template <int FORM>
+template <int FORM, int MAP = 0>
 __global__ void __launch_bounds__(256) fill_mrg_tma_kernel(const FillParams p, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (smem_addr(smem_raw) + 1023u) & ~1023u;
@@ -86,7 +97,7 @@ __global__ void __launch_bounds__(256) fill_mrg_tma_kernel(const FillParams p, c
     uint64_t v[kChunk];
     const uint64_t left = p.per_stream - x0;
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) v[j] = ((uint64_t)j < left) ? mrg_next_output<FORM>(g, rej, p) : 0ull;
+    for (int j = 0; j < kChunk; ++j) v[j] = ((uint64_t)j < left) ? mrg_next_output<FORM, MAP>(g, rej, p) : 0ull;
     if (lane == 0) bulk_wait_read<0>();
     __syncwarp();
 #pragma unroll
@@ -107,14 +118,14 @@ __global__ void __launch_bounds__(256) fill_mrg_tma_kernel(const FillParams p, c
 }
 
 // Plain stores (any alignment, host-mapped outputs): each thread writes its own stream.
-template <int FORM>
+template <int FORM, int MAP = 0>
 __global__ void __launch_bounds__(256) fill_mrg_plain_kernel(const FillParams p) {
   const uint64_t stream = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (stream >= p.n_streams) return;
   Mrg32k3a g = mrg_load(p.state, stream);
   uint32_t rej = 0;
   uint64_t* dst = p.out + stream * p.per_stream;
-  for (uint64_t i = 0; i < p.per_stream; ++i) dst[i] = mrg_next_output<FORM>(g, rej, p);
+  for (uint64_t i = 0; i < p.per_stream; ++i) dst[i] = mrg_next_output<FORM, MAP>(g, rej, p);
   mrg_store(p.state, stream, g);
   if (p.rejects) p.rejects[stream] = rej;
 }
@@ -139,11 +150,11 @@ namespace {
 constexpr int kWarpsPerBlock = 8;
 constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * prngd::kTileBytes + 1024;
 
-template <int FORM>
+template <int FORM, int MAP = 0>
 cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, cudaStream_t s) {
   const unsigned blocks = (unsigned)((p.n_streams + 255) / 256);
   if (map) {
-    auto k = prngd::fill_mrg_tma_kernel<FORM>;
+    auto k = prngd::fill_mrg_tma_kernel<FORM, MAP>;
     static bool attr = false;
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
@@ -152,7 +163,7 @@ cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, 
     }
     k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
   } else {
-    prngd::fill_mrg_plain_kernel<FORM><<<blocks, 256, 0, s>>>(p);
+    prngd::fill_mrg_plain_kernel<FORM, MAP><<<blocks, 256, 0, s>>>(p);
   }
   return cudaGetLastError();
 }
@@ -161,7 +172,8 @@ cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, 
 int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                     uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode) {
   if (n_streams == 0 || per_stream == 0) return PRNG_OK;
-  // PRNG_MODE_BALANCED changes no value, and the MRG conversion has no such route: ignored
+  // PRNG_MODE_BALANCED changes no value: it selects form B's FP64 rounding route (form A's MRG
+  // conversion is the instruction already)
   if ((mode & ~PRNG_MODE_BALANCED) != 0 ||
       (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR))
     return fail(PRNG_EINVAL, "MRG32k3a streams take forms A, B and C with mode 0");
@@ -183,7 +195,10 @@ int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, ui
   switch (form) {
     case PRNG_FORM_A_FP64: e = launch_mrg_form<prngd::kFormA>(p, mp, s); break;
     case PRNG_FORM_C_F32PAIR: e = launch_mrg_form<prngd::kFormC>(p, mp, s); break;
-    default: e = launch_mrg_form<prngd::kFormB>(p, mp, s); break;
+    default:
+      e = (mode & PRNG_MODE_BALANCED) ? launch_mrg_form<prngd::kFormB, prngd::kMapCvt>(p, mp, s)
+                                      : launch_mrg_form<prngd::kFormB>(p, mp, s);
+      break;
   }
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "MRG32k3a fill launch: %s", cudaGetErrorString(e));
   return PRNG_OK;

@@ -42,4 +42,22 @@ PRNGD_HD uint32_t mrg_next(Mrg32k3a& g) {
   return p1 > p2 ? p1 - p2 : p1 - p2 + kMrgM1;
 }
 
+// Fast path of floor(V 2^64), V = n / D, D = (m1 - 1)^2 = (2^32 - 210)^2, n = A m1 + B < 2^64.
+// With c = 210 2^-32, 2^64 / D = sum (i + 1) c^i, so with n = nh 2^32 + nl
+//   V 2^64 = n + E0 + E1 2^-32 + E2 2^-64 + eps,
+//   E0 = 420 nh, E1 = 420 nl + 132300 nh, E2 = 132300 nl + 37044000 nh,
+// 0 <= eps < 5.4e-10 (37044000 nl 2^-96 and the terms from 5 c^4 n on). With S = E1 + (E2 >> 32)
+// the exact value is n + E0 + (S + r) 2^-32 with 0 <= r < 3.3, so the integer part is
+// n + E0 + (S >> 32) unless the low word of S lies within 16 of 2^32 (`ok` = 0). For A >= 2^22
+// it is at least 2^54, and it rounds like the xorshift fast path's I.
+PRNGD_HD uint64_t mrg_fast_I(uint64_t n, uint32_t& ok) {
+  const uint64_t nh = n >> 32, nl = n & 0xFFFFFFFFull;
+  const uint64_t E0 = 420u * nh;
+  const uint64_t E1 = 420u * nl + 132300u * nh;
+  const uint64_t E2 = 132300u * nl + 37044000u * nh;
+  const uint64_t S = E1 + (E2 >> 32);
+  ok = ((uint32_t)S < 0xFFFFFFF0u) ? 1u : 0u;
+  return n + E0 + (S >> 32);
+}
+
 }  // namespace prngd

@@ -46,6 +46,41 @@ int main() {
     }
     run(st, 3);
   }
+  // the conversion's fast path: floor(n 2^64 / D) exactly wherever it reports ok, on random n,
+  // on n of each binade's ends, and on n placing the low word of S next to 2^32
+  const unsigned __int128 D = (unsigned __int128)(m1 - 1u) * (m1 - 1u);
+  auto check_fast = [&](uint64_t n) {
+    if (n == 0 || (unsigned __int128)n >= D) return;
+    uint32_t ok;
+    const uint64_t I = mrg_fast_I(n, ok);
+    if (!ok) return;
+    ++checked;
+    const uint64_t want = (uint64_t)(((unsigned __int128)n << 64) / D);
+    if (I != want) {
+      if (bad < 10) printf("mrg_fast_I mismatch n=%llu\n", (unsigned long long)n);
+      ++bad;
+    }
+  };
+  for (int i = 0; i < 4000000; ++i) check_fast(rng() % (uint64_t)((m1 - 1ull) * (m1 - 1ull)));
+  for (int p = 54; p < 64; ++p)
+    for (int d = -64; d < 64; ++d) check_fast((1ull << p) + (uint64_t)(int64_t)d);
+  long near = 0;
+  for (int i = 0; i < 400000; ++i) {  // nl solving 420 nl = k 2^32 - (132300 nh mod 2^32) - d: S's low
+    const uint64_t nh = rng() % (m1 - 2u);       // word lands within a few hundred of 2^32
+    const uint64_t k = 1 + rng() % 419, d = rng() % 600;
+    uint64_t nl = 0;
+    for (int it = 0; it < 2; ++it) {  // the carry term (E2 >> 32) depends on nl: refine once
+      const uint64_t e = (132300u * nl + 37044000u * nh) >> 32;
+      const int64_t num = (int64_t)((k << 32) - ((132300u * nh + e) & 0xFFFFFFFFull)) - (int64_t)d;
+      nl = num < 0 ? (1ull << 40) : (uint64_t)num / 420u;
+    }
+    if (nl > 0xFFFFFFFFull) continue;
+    const uint64_t n = (nh << 32) | nl;
+    const uint64_t S = 420u * nl + 132300u * nh + ((132300u * nl + 37044000u * nh) >> 32);
+    if ((uint32_t)S >= 0xFFFFF000u) ++near;
+    check_fast(n);
+  }
+  printf("near-margin samples %ld\n", near);
   printf("checked %ld bad %ld\n", checked, bad);
   return bad != 0;
 }

@@ -18,16 +18,20 @@ def same(a, b):
     return np.array_equal(np.ascontiguousarray(a).view(np.uint8), np.ascontiguousarray(b).view(np.uint8))
 
 
-@pytest.mark.parametrize("form", [P.FORM_B_INTBITS, P.FORM_A_FP64, P.FORM_C_F32PAIR])
+@pytest.mark.parametrize("form,mode", [(P.FORM_B_INTBITS, 0), (P.FORM_A_FP64, 0), (P.FORM_C_F32PAIR, 0),
+                                       (P.FORM_B_INTBITS, P.MODE_BALANCED)])
 @pytest.mark.parametrize("per,offset", [(1030, 0), (333, 0), (64, 1)])
-def test_mrg_fill_matches_the_oracle(form, per, offset):
+def test_mrg_fill_matches_the_oracle(form, mode, per, offset):
+    """Every output and reject count against the oracle (the series fast path, its margin
+    fallback and the exact division all reach it at these sizes; PRNG_MODE_BALANCED changes no
+    value)."""
     seed, ns = 21, 100
     with P.Generator(seed, ns, generator=P.GEN_MRG32K3A) as g:
         assert g.generator == P.GEN_MRG32K3A
         buf = torch.zeros(ns * per + offset + 2, dtype=torch.float64, device="cuda")
         out = buf[offset:offset + ns * per]
         rej = torch.full((ns,), 5, dtype=torch.int64, device="cuda")
-        g.fill_mode(out, per, form, 0, rej)
+        g.fill_mode(out, per, form, mode, rej)
         got = out.cpu().numpy()
         got = got.view(np.float32) if form == P.FORM_C_F32PAIR else got
     want, wrej = O.fill_mrg(seed, 0, ns, per, OF[form])
@@ -86,12 +90,13 @@ def test_mrg_refuses_xorshift_only_paths():
             assert e.value.code == P.PRNG_EINVAL
 
 
-def test_mrg_bulk_sampled():
+@pytest.mark.parametrize("mode", [0, P.MODE_BALANCED])
+def test_mrg_bulk_sampled(mode):
     """2^20 streams x 1024 outputs (the bulk size), form B: 24 streams against the oracle."""
     seed, ns, per = 1, 2**20, 1024
     with P.Generator(seed, ns, generator=P.GEN_MRG32K3A) as g:
         out = torch.empty(ns * per, dtype=torch.float64, device="cuda")
-        g.fill_f64(out, per, P.FORM_B_INTBITS)
+        g.fill_mode(out, per, P.FORM_B_INTBITS, mode)
         torch.cuda.synchronize()
         for s in [0, ns - 1] + [int(v) for v in np.random.default_rng(1).integers(0, ns, 22)]:
             want, _ = O.fill_mrg(seed, s, 1, per, O.FORM_B)

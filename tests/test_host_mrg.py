@@ -23,3 +23,5 @@ def test_mrg_step_matches_oracle(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:]
     assert "bad 0" in out.stdout
+    near = int(out.stdout.split("near-margin samples")[1].split()[0])
+    assert near > 10000, near  # the fast path's margin was reached
