@@ -15,17 +15,23 @@ struct Mrg32k3a {
   uint32_t b0, b1, b2;  // x2_{n-3}, x2_{n-2}, x2_{n-1}
 };
 
-// v mod m1 for v < 2^54, folding 2^32 = 209 (mod m1) twice.
+// v mod m1 for v < 2^54, folding 2^32 = 209 (mod m1): one wide fold leaves w < 2^32 + 2^30, so
+// the second fold is a 32-bit add of 0 or 209 (its low word is below 2^30 when its high word
+// is 1, so the add does not carry).
 PRNGD_HD uint32_t mod_m1(uint64_t v) {
-  v = (v >> 32) * 209u + (v & 0xFFFFFFFFull);  // < 2^32 + 2^30
-  v = (v >> 32) * 209u + (v & 0xFFFFFFFFull);  // < 2^32 + 209
-  return (uint32_t)(v >= kMrgM1 ? v - kMrgM1 : v);
+  const uint64_t w = (v >> 32) * 209u + (v & 0xFFFFFFFFull);
+  const uint32_t r = (uint32_t)w + ((uint32_t)(w >> 32) ? 209u : 0u);
+  return r >= kMrgM1 ? r - kMrgM1 : r;
 }
-// v mod m2 for v < 2^54, folding 2^32 = 22853 (mod m2).
+// v mod m2 for v < 2^54, folding 2^32 = 22853 (mod m2): after one wide fold w < 2^37, whose
+// high word (< 32) folds with a 32-bit multiply; a carry out of that add (the sum then < 2^20)
+// folds once more.
 PRNGD_HD uint32_t mod_m2(uint64_t v) {
-  v = (v >> 32) * 22853u + (v & 0xFFFFFFFFull);  // < 2^37
-  v = (v >> 32) * 22853u + (v & 0xFFFFFFFFull);  // < 2^32 + 2^19
-  return (uint32_t)(v >= kMrgM2 ? v - kMrgM2 : v);
+  const uint64_t w = (v >> 32) * 22853u + (v & 0xFFFFFFFFull);
+  const uint32_t t = (uint32_t)(w >> 32) * 22853u;  // < 2^20
+  uint32_t r = (uint32_t)w + t;
+  if (r < t) r += 22853u;
+  return r >= kMrgM2 ? r - kMrgM2 : r;
 }
 
 // One step; returns z in [1, m1]. The negative terms are made positive by adding a multiple of

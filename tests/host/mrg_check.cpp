@@ -46,6 +46,23 @@ int main() {
     }
     run(st, 3);
   }
+  // the reductions against %, for v < 2^54: random, and at multiples of 2^32, m1 and m2 +- small
+  auto check_mod = [&](uint64_t v) {
+    if (v >> 54) return;  // outside the reductions' domain (k = 0, d < 0 wraps)
+    ++checked;
+    if (mod_m1(v) != (uint32_t)(v % m1) || mod_m2(v) != (uint32_t)(v % m2)) {
+      if (bad < 10) printf("mod mismatch v=%llu\n", (unsigned long long)v);
+      ++bad;
+    }
+  };
+  for (int i = 0; i < 4000000; ++i) check_mod(rng() >> 10);
+  for (uint64_t k = 0; k < (1ull << 22); k += 1 + (k >> 6))
+    for (int d = -3; d <= 3; ++d) {
+      check_mod((k << 32) + (uint64_t)(int64_t)d);
+      check_mod(k * m1 + (uint64_t)(int64_t)d);
+      check_mod(k * m2 + (uint64_t)(int64_t)d);
+    }
+  check_mod((1ull << 54) - 1);
   // the conversion's fast path: floor(n 2^64 / D) exactly wherever it reports ok, on random n,
   // on n of each binade's ends, and on n placing the low word of S next to 2^32
   const unsigned __int128 D = (unsigned __int128)(m1 - 1u) * (m1 - 1u);
