@@ -15,12 +15,13 @@ struct Mrg32k3a {
   uint32_t b0, b1, b2;  // x2_{n-3}, x2_{n-2}, x2_{n-1}
 };
 
-// v mod m1 for v < 2^54, folding 2^32 = 209 (mod m1): one wide fold leaves w < 2^32 + 2^30, so
-// the second fold is a 32-bit add of 0 or 209 (its low word is below 2^30 when its high word
-// is 1, so the add does not carry).
+// v mod m1 for v < 2^54, folding 2^32 = 209 (mod m1) in 32-bit arithmetic: the high word times
+// 209 is below 2^30, and a carry out of adding it to the low word (the sum then < 2^30) folds
+// once more as + 209.
 PRNGD_HD uint32_t mod_m1(uint64_t v) {
-  const uint64_t w = (v >> 32) * 209u + (v & 0xFFFFFFFFull);
-  const uint32_t r = (uint32_t)w + ((uint32_t)(w >> 32) ? 209u : 0u);
+  const uint32_t t = (uint32_t)(v >> 32) * 209u;
+  uint32_t r = (uint32_t)v + t;
+  if (r < t) r += 209u;
   return r >= kMrgM1 ? r - kMrgM1 : r;
 }
 // v mod m2 for v < 2^54, folding 2^32 = 22853 (mod m2): after one wide fold w < 2^37, whose
