@@ -124,8 +124,10 @@ int prng_get_info(prng_t h, uint64_t* n_streams, int* w);
  * PRNG_FORM_B_INTBITS. d_out: device pointer to n_streams * per_stream doubles (8-byte
  * aligned; 16-byte alignment and an even per_stream select the TMA store path).
  * d_rejects (nullable): device pointer to n_streams uint64, set to the number of rejected
- * pairs each stream consumed in this call. per_stream == 0 is a no-op.
- * Errors: PRNG_EINVAL (null handle or d_out, misaligned d_out, bad form), PRNG_ECUDA.
+ * pairs each stream consumed in this call (8-byte aligned). per_stream == 0 is a no-op.
+ * n_streams * per_stream may not exceed 2^60 outputs (every byte offset fits in 64 bits).
+ * Errors: PRNG_EINVAL (null handle or d_out, misaligned d_out or d_rejects, bad form, more
+ * than 2^60 outputs), PRNG_ECUDA.
  */
 int prng_fill_f64(prng_t h, double* d_out, uint64_t per_stream, int form, uint64_t* d_rejects,
                   void* cuda_stream);
@@ -161,8 +163,8 @@ int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_r
  * give exactly the outputs of prng_fill_f64 / prng_fill_f32pair. The streams advance as the
  * reject rule consumes draws. d_out: device memory, 8-byte aligned; the fast (TMA) path needs
  * 16-byte alignment and an even per_stream.
- * Errors: PRNG_EINVAL (null handle or d_out, misaligned d_out, unknown form or mode bits),
- * PRNG_ECUDA.
+ * Errors: PRNG_EINVAL (null handle or d_out, misaligned d_out or d_rejects, unknown form or
+ * mode bits, more than 2^60 outputs), PRNG_ECUDA.
  */
 int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mode, uint64_t* d_rejects,
                    void* cuda_stream);
@@ -294,14 +296,14 @@ typedef struct prng_request {
   int32_t kind;          /* PRNG_REQ_FRESH or PRNG_REQ_RESIDENT */
   int32_t form;          /* PRNG_FORM_A_FP64, PRNG_FORM_B_INTBITS, PRNG_FORM_C_F32PAIR or
                             PRNG_FORM_L_ALGO1 */
-  uint64_t length;       /* outputs, >= 1 */
+  uint64_t length;       /* outputs, 1 .. 2^60 */
   uint64_t seed;         /* FRESH: seed of the request's streams */
   uint64_t first_stream; /* FRESH: first stream id; RESIDENT: first stream of the handle */
   uint64_t n_streams;    /* RESIDENT: streams of the handle to continue (FRESH: ignored) */
   uint32_t chunk;        /* FRESH: outputs per stream, even (0 = 1024); RESIDENT: ignored */
   uint32_t mode;         /* PRNG_MODE_* bits as for prng_fill_mode (0: Eq. 4, pair rejects) */
   void* d_out;           /* device pointer, 16-byte aligned */
-  uint64_t* d_rejects;   /* nullable device pointer, one count per row */
+  uint64_t* d_rejects;   /* nullable device pointer, 8-byte aligned, one count per row */
 } prng_request;
 
 /*

@@ -233,6 +233,13 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
   return PRNG_OK;
 }
 
+int check_fill_extent(prng_ctx* h, uint64_t per_stream, const void* d_rejects) {
+  if ((uintptr_t)d_rejects & 7) return fail(PRNG_EINVAL, "d_rejects must be 8-byte aligned");
+  if (per_stream > kMaxOutputs / h->n_streams)
+    return fail(PRNG_EINVAL, "n_streams * per_stream exceeds 2^60 outputs");
+  return PRNG_OK;
+}
+
 int check_handle_device(prng_ctx* h) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -323,7 +330,8 @@ int prng_fill_f64(prng_t h, double* d_out, uint64_t per_stream, int form, uint64
   if (per_stream == 0) return PRNG_OK;
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
-  int rc = check_handle_device(h);
+  int rc = check_fill_extent(h, per_stream, d_rejects);
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, form, d_rejects, (cudaStream_t)cuda_stream,
                      true);
@@ -334,7 +342,8 @@ int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_r
   if (per_stream == 0) return PRNG_OK;
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
-  int rc = check_handle_device(h);
+  int rc = check_fill_extent(h, per_stream, d_rejects);
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, PRNG_FORM_C_F32PAIR, d_rejects,
                      (cudaStream_t)cuda_stream, true);
@@ -350,7 +359,8 @@ int prng_fill_mode(prng_t h, void* d_out, uint64_t per_stream, int form, int mod
   if (per_stream == 0) return PRNG_OK;
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
-  int rc = check_handle_device(h);
+  int rc = check_fill_extent(h, per_stream, d_rejects);
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return launch_fill(h, h->d_state, h->n_streams, d_out, per_stream, form, d_rejects, (cudaStream_t)cuda_stream,
                      true, mode);
@@ -362,7 +372,7 @@ size_t prng_state_bytes(prng_t h) {
 
 int prng_state_save(prng_t h, void* host_buf, size_t bytes) {
   if (!h || !host_buf) return fail(PRNG_EINVAL, "null argument");
-  if (bytes != prng_state_bytes(h)) return fail(PRNG_EINVAL, "bytes must be n_streams * 16");
+  if (bytes != prng_state_bytes(h)) return fail(PRNG_EINVAL, "bytes must be prng_state_bytes(h)");
   cudaError_t e = cudaMemcpy(host_buf, h->d_state, bytes, cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "state save: %s", cudaGetErrorString(e));
   return PRNG_OK;
@@ -370,7 +380,7 @@ int prng_state_save(prng_t h, void* host_buf, size_t bytes) {
 
 int prng_state_restore(prng_t h, const void* host_buf, size_t bytes) {
   if (!h || !host_buf) return fail(PRNG_EINVAL, "null argument");
-  if (bytes != prng_state_bytes(h)) return fail(PRNG_EINVAL, "bytes must be n_streams * 16");
+  if (bytes != prng_state_bytes(h)) return fail(PRNG_EINVAL, "bytes must be prng_state_bytes(h)");
   cudaError_t e = cudaMemcpy(h->d_state, host_buf, bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "state restore: %s", cudaGetErrorString(e));
   return PRNG_OK;
@@ -382,7 +392,8 @@ int prng_fill_f64_host(prng_t h, double* host_out, uint64_t per_stream, int form
     return fail(PRNG_EINVAL, "prng_fill_f64_host takes form A (0) or B (1), got %d", form);
   if (per_stream == 0) return PRNG_OK;
   if (!host_out) return fail(PRNG_EINVAL, "host_out is NULL");
-  int rc = check_handle_device(h);
+  int rc = check_fill_extent(h, per_stream, nullptr);
+  if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return host_fill(h, host_out, per_stream, form, host_rejects);
 }

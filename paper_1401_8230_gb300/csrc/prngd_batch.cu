@@ -185,7 +185,9 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
   if (r.mode & ~(uint32_t)kAllModes) return fail(PRNG_EINVAL, "request mode %u", r.mode);
   d.mode = (uint16_t)r.mode;
   if (r.length == 0) return fail(PRNG_EINVAL, "request length 0");
+  if (r.length > kMaxOutputs) return fail(PRNG_EINVAL, "request length exceeds 2^60 outputs");
   if (!r.d_out || ((uintptr_t)r.d_out & 15)) return fail(PRNG_EINVAL, "request d_out must be 16-byte aligned");
+  if ((uintptr_t)r.d_rejects & 7) return fail(PRNG_EINVAL, "request d_rejects must be 8-byte aligned");
   d.length = r.length;
   d.out = (uint64_t*)r.d_out;
   d.rejects = r.d_rejects;

@@ -51,6 +51,10 @@ struct prng_ctx {
 namespace prngd_host {
 int fail(int code, const char* fmt, ...);
 int check_handle_device(prng_ctx* h);
+// Output arguments of a fill: a device rejects array (nullable) of 8-byte aligned words, and at
+// most 2^60 outputs in all (n_streams * per_stream), so that every byte offset fits in 64 bits.
+int check_fill_extent(prng_ctx* h, uint64_t per_stream, const void* d_rejects);
+constexpr uint64_t kMaxOutputs = 1ull << 60;
 int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,
                 uint64_t* rejects, cudaStream_t s, bool allow_tma, int mode = 0);
 // Every PRNG_MODE_* bit an entry point accepts.

@@ -407,6 +407,7 @@ int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mo
   if (!d_out) return fail(PRNG_EINVAL, "d_out is NULL");
   if ((uintptr_t)d_out & 7) return fail(PRNG_EINVAL, "d_out must be 8-byte aligned");
   int rc = require_xorshift(h, "prng_fill_split");
+  if (!rc) rc = check_fill_extent(h, per_stream, d_rejects);
   if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return fill_split(h, d_out, per_stream, form, mode, segments, d_rejects, (cudaStream_t)cuda_stream);

@@ -72,6 +72,7 @@ extern "C" int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist,
   if (((uintptr_t)d_hist & 7) || ((uintptr_t)d_sums & 7)) return fail(PRNG_EINVAL, "d_hist/d_sums must be 8-byte aligned");
   if (per_stream == 0) return PRNG_OK;
   int rc = require_xorshift(h, "prng_fused_stats");
+  if (!rc) rc = check_fill_extent(h, per_stream, d_rejects);
   if (!rc) rc = check_handle_device(h);
   if (rc) return rc;
   return launch_stats(h, per_stream, d_hist, d_sums, d_rejects, (cudaStream_t)cuda_stream);

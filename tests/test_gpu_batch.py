@@ -155,6 +155,12 @@ def test_batch_errors():
         with pytest.raises(P.PrngError) as e:  # odd chunk
             P.prng_submit(g.h, [P.fresh_request(b, 10, 1, 0, 1, 3)])
         assert e.value.code == P.PRNG_EINVAL
+        rej = torch.zeros(8, dtype=torch.int64, device="cuda")
+        for req in (P.fresh_request(b, 10, 1, 0, rejects=rej.data_ptr() + 4),  # misaligned rejects
+                    P.fresh_request(b, 2**60 + 1, 1, 0)):  # more than 2^60 outputs
+            with pytest.raises(P.PrngError) as e:
+                P.prng_submit(g.h, [req])
+            assert e.value.code == P.PRNG_EINVAL
         with pytest.raises(P.PrngError) as e:
             P.prng_poll(g.h, 12345)
         assert e.value.code == P.PRNG_ENOTFOUND

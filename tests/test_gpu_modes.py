@@ -138,6 +138,36 @@ def test_bad_arguments():
             g.fill_f64(buf, 16, P.FORM_L_ALGO1)
 
 
+def test_extent_and_rejects_checks():
+    """A misaligned d_rejects and more than 2^60 outputs in all (n_streams * per_stream) are
+    refused by every fill entry point before anything is launched; the streams do not move."""
+    ns = 32
+    with P.Generator(1, ns, 32) as g:
+        buf = torch.zeros(ns * 16, dtype=torch.float64, device="cuda")
+        rej = torch.zeros(ns + 1, dtype=torch.int64, device="cuda")
+        hist = torch.zeros(65536, dtype=torch.int64, device="cuda")
+        sums = torch.zeros(8, dtype=torch.int64, device="cuda")
+        before = np.zeros(P.prng_state_bytes(g.h), dtype=np.uint8)
+        g.state_save(before)
+        huge = 2**60 // ns + 1
+        calls = [lambda per, r: g.fill_f64(buf, per, P.FORM_B_INTBITS, r),
+                 lambda per, r: g.fill_f32pair(buf, per, r),
+                 lambda per, r: g.fill_mode(buf, per, P.FORM_B_INTBITS, F, r),
+                 lambda per, r: g.fill_split(buf, per, P.FORM_B_INTBITS, 0, 0, r),
+                 lambda per, r: g.fused_stats(per, hist, sums, r)]
+        for call in calls:
+            for per, r in [(16, rej.data_ptr() + 4), (huge, None), (huge, rej)]:
+                with pytest.raises(P.PrngError) as e:
+                    call(per, r)
+                assert e.value.code == P.PRNG_EINVAL
+        with pytest.raises(P.PrngError) as e:
+            g.fill_f64_host(np.zeros(16), huge)
+        assert e.value.code == P.PRNG_EINVAL
+        after = np.zeros_like(before)
+        g.state_save(after)
+        assert np.array_equal(before, after)
+
+
 @pytest.mark.parametrize("mode", [P.MODE_EQ5, P.MODE_EQ5 | P.MODE_ONE_MINUS, P.MODE_ONE_MINUS, F, F | P.MODE_EQ5])
 def test_bulk_configuration_sampled(mode):
     """2^20 streams x 1024 outputs (8 GiB), w = 32, form B, in the launch the bench times; 48
