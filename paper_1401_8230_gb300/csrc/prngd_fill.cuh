@@ -203,6 +203,15 @@ __device__ __forceinline__ void xs_block4(XorShift128& s) {
   s.w = xs_word(s.w, s.z);
 }
 
+// ~u as u * (-1) - 1, a multiply-add by the run-time -1 (`neg_one` = 0 - FillParams::one), so
+// that the complement of the 1 - z map runs on the FMA pipe instead of adding an ALU operation
+// per draw to the pipe that bounds the pair path.
+__device__ __forceinline__ uint32_t complement_fma(uint32_t u, uint32_t neg_one) {
+  uint32_t c;
+  asm("mad.lo.u32 %0, %1, %2, -1;" : "=r"(c) : "r"(u), "r"(neg_one));
+  return c;
+}
+
 // The w = 32 fast paths written out as PTX (Eq. 4: fast32_ok / fast32_bits; Eq. 5:
 // fast32_eq5_ok / fast32_eq5_bits) in two steps: the 64-bit I = floor(V 2^64) and the check,
 // then the rounding of I to the output's bits (bits_from_I_int or bits_from_I_cvt). The adds
@@ -490,8 +499,9 @@ __device__ __forceinline__ void next_pair(XorShift128& st, uint32_t& rej, const 
   // 1 - z: the arithmetic runs on the complemented draws (the state itself is not changed);
   // complementing the 32-bit word complements its top w bits.
   constexpr bool kComp = (MAP & kMapOneMinus) != 0;
-  const uint32_t dx = kComp ? ~st.x : st.x, dy = kComp ? ~st.y : st.y;
-  const uint32_t dz = kComp ? ~st.z : st.z, dw = kComp ? ~st.w : st.w;
+  const uint32_t neg_one = 0u - p.one;
+  const uint32_t dx = kComp ? complement_fma(st.x, neg_one) : st.x, dy = kComp ? complement_fma(st.y, neg_one) : st.y;
+  const uint32_t dz = kComp ? complement_fma(st.z, neg_one) : st.z, dw = kComp ? complement_fma(st.w, neg_one) : st.w;
   uint32_t ok;
   if constexpr ((MAP & kMapEq5) != 0) {
     // Eq. 5. Small values take the inline medium path (w = 32 and 24); rejects and boundary
