@@ -70,10 +70,15 @@ int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint
     const int b = k & 1;
     int rc = launch_fill(h, state_at(h, s0), cnt, h->d_stage[b], per_stream, form,
                          host_rejects ? h->d_rej_stage + s0 : nullptr, h->io_stream[b], true);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(host_out + s0 * per_stream, h->d_stage[b], (size_t)cnt * row, cudaMemcpyDeviceToHost,
-                        h->io_stream[b]);
-    if (e != cudaSuccess) return fail(PRNG_ECUDA, "copy to host: %s", cudaGetErrorString(e));
+    if (!rc) {
+      e = cudaMemcpyAsync(host_out + s0 * per_stream, h->d_stage[b], (size_t)cnt * row, cudaMemcpyDeviceToHost,
+                          h->io_stream[b]);
+      if (e != cudaSuccess) rc = fail(PRNG_ECUDA, "copy to host: %s", cudaGetErrorString(e));
+    }
+    if (rc) {  // the copies already queued write into host_out: let them end before returning
+      for (int q = 0; q < 2; ++q) cudaStreamSynchronize(h->io_stream[q]);
+      return rc;
+    }
   }
   for (int b = 0; b < 2; ++b) {
     e = cudaStreamSynchronize(h->io_stream[b]);

@@ -77,12 +77,17 @@ extern "C" int prng_fill_f64_host_noalloc(prng_t h, double* host_out, uint64_t p
     const uint64_t cnt = (h->n_streams - s0 < slice) ? h->n_streams - s0 : slice;
     rc = prngd_host::launch_fill(h, prngd_host::state_at(h, s0), cnt, d_values, per_stream, form,
                                  host_rejects ? d_rej : nullptr, s, true);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(host_out + s0 * per_stream, d_values, (size_t)cnt * per_stream * 8, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return fail(PRNG_ECUDA, "copy to host: %s", cudaGetErrorString(e));
-    if (host_rejects) {
+    if (!rc) {
+      e = cudaMemcpyAsync(host_out + s0 * per_stream, d_values, (size_t)cnt * per_stream * 8, cudaMemcpyDeviceToHost, s);
+      if (e != cudaSuccess) rc = fail(PRNG_ECUDA, "copy to host: %s", cudaGetErrorString(e));
+    }
+    if (!rc && host_rejects) {
       e = cudaMemcpyAsync(host_rejects + s0, d_rej, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s);
-      if (e != cudaSuccess) return fail(PRNG_ECUDA, "reject copy: %s", cudaGetErrorString(e));
+      if (e != cudaSuccess) rc = fail(PRNG_ECUDA, "reject copy: %s", cudaGetErrorString(e));
+    }
+    if (rc) {  // the copies already queued write into host memory: let them end before returning
+      cudaStreamSynchronize(s);
+      return rc;
     }
   }
   e = cudaStreamSynchronize(s);

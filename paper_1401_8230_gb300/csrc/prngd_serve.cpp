@@ -262,8 +262,8 @@ int prng_server_submit_mode(prng_server_t s, uint64_t client, uint64_t length, i
       form != PRNG_FORM_L_ALGO1)
     return fail(PRNG_EINVAL, "form %d", form);
   if (mode & ~(uint32_t)prngd_host::kAllModes) return fail(PRNG_EINVAL, "mode %u", mode);
+  if (length > s->pool.size() / 8) return fail(PRNG_EINVAL, "request larger than the whole pool");
   const size_t bytes = (size_t)length * 8;
-  if (bytes > s->pool.size()) return fail(PRNG_EINVAL, "request larger than the whole pool");
   const size_t off = s->pool.alloc(bytes);
   if (off == SIZE_MAX) return fail(PRNG_EBUSY, "output pool full (%zu of %zu bytes in use)", s->pool.used(), s->pool.size());
   Req r;

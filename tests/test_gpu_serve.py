@@ -114,9 +114,10 @@ def test_admission_budget_and_trace_replay():
             with pytest.raises(P.PrngError) as e:
                 P.prng_server_submit(srv, 1, 100000)
             assert e.value.code == P.PRNG_EBUSY
-            with pytest.raises(P.PrngError) as e:  # larger than the pool
-                P.prng_server_submit(srv, 1, 200000)
-            assert e.value.code == P.PRNG_EINVAL
+            for length in (200000, 2**61 + 1):  # larger than the pool (the second wraps 8 * length)
+                with pytest.raises(P.PrngError) as e:
+                    P.prng_server_submit(srv, 1, length)
+                assert e.value.code == P.PRNG_EINVAL
             with pytest.raises(P.PrngError):  # not finished yet or not launched: cannot release
                 P.prng_server_release(srv, a)
             P.prng_server_drain(srv, 30)
