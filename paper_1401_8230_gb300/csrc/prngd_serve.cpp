@@ -8,10 +8,13 @@
 // on the device at a time; later requests of a busy client wait in order.
 //
 // Batching: step() puts every admitted request whose client is idle into the next batch
-// (small and large requests go to two separate CUDA streams, so small requests do not wait
-// behind large ones) and harvests finished batches. Requests that arrive while batches run
-// are admitted as soon as pool memory allows and join the next batch; batches overlap on
-// the device.
+// (small and large requests go to two separate lanes, so small requests do not wait behind
+// large ones) and harvests finished batches. Requests that arrive while batches run are
+// admitted as soon as pool memory allows and join the next batch. Within a lane, successive
+// batches rotate over several CUDA streams: no two batches in flight share a client (hence
+// a stream of the handle), so they need no order, and a batch whose last long rows are still
+// running no longer holds the next one back (a 2^28-output request of a 16384-stream client
+// has rows of 16384 outputs, a few milliseconds of one warp's work).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -96,6 +99,7 @@ struct Req {
 };
 
 constexpr int kLanes = 2;                      // small / large requests
+constexpr int kStreamsPerLane = 3;             // CUDA streams a lane's batches rotate over
 constexpr int kMaxBatchesPerLane = 6;          // batches of one lane on the device at once
 constexpr uint64_t kLargeOutputs = 1ull << 20;  // requests above this go to the large lane
 
@@ -105,7 +109,8 @@ struct prng_server {
   prng_t h = nullptr;
   uint64_t S = 0, min_per = 0, n_clients = 0;
   Pool pool;
-  cudaStream_t lane_stream[kLanes] = {nullptr, nullptr};
+  cudaStream_t lane_stream[kLanes][kStreamsPerLane] = {};
+  int lane_next[kLanes] = {};  // stream of the lane's next batch
   uint64_t next_id = 1;
   std::unordered_map<uint64_t, Req> reqs;
   std::deque<uint64_t> waiting[kLanes];              // admitted, not launched (arrival order)
@@ -181,7 +186,7 @@ int launch_lane(prng_server* s, int lane) {
   s->waiting[lane] = std::move(keep);
   if (batch.empty()) return PRNG_OK;
   uint64_t ticket = 0;
-  int rc = prng_submit(s->h, batch.data(), (int)batch.size(), &ticket, s->lane_stream[lane]);
+  int rc = prng_submit(s->h, batch.data(), (int)batch.size(), &ticket, s->lane_stream[lane][s->lane_next[lane]]);
   if (rc == PRNG_EBUSY) {  // no free batch slot: put them back in front, in order
     for (size_t i = ids.size(); i-- > 0;) s->waiting[lane].push_front(ids[i]);
     return PRNG_OK;
@@ -198,6 +203,7 @@ int launch_lane(prng_server* s, int lane) {
   }
   s->inflight.push_back({ticket, lane, ids});
   s->launched_batches++;
+  s->lane_next[lane] = (s->lane_next[lane] + 1) % kStreamsPerLane;
   return PRNG_OK;
 }
 
@@ -229,21 +235,26 @@ int prng_server_create(prng_server_t* out, prng_t h, uint64_t streams_per_client
     return fail(PRNG_ENOMEM, "output pool of %zu bytes", pool_bytes);
   }
   for (int l = 0; l < kLanes; ++l)
-    if (cudaStreamCreateWithFlags(&s->lane_stream[l], cudaStreamNonBlocking) != cudaSuccess) {
-      for (int k = 0; k < l; ++k) cudaStreamDestroy(s->lane_stream[k]);
-      delete s;
-      return fail(PRNG_ECUDA, "stream creation");
-    }
+    for (int k = 0; k < kStreamsPerLane; ++k)
+      if (cudaStreamCreateWithFlags(&s->lane_stream[l][k], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        for (auto& lane : s->lane_stream)
+          for (auto& st : lane)
+            if (st) cudaStreamDestroy(st);
+        delete s;
+        return fail(PRNG_ECUDA, "stream creation");
+      }
   *out = s;
   return PRNG_OK;
 }
 
 int prng_server_destroy(prng_server_t s) {
   if (!s) return PRNG_OK;
-  for (int l = 0; l < kLanes; ++l) {
-    cudaStreamSynchronize(s->lane_stream[l]);
-    cudaStreamDestroy(s->lane_stream[l]);
-  }
+  for (auto& lane : s->lane_stream)
+    for (auto& st : lane) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
   delete s;
   return PRNG_OK;
 }
