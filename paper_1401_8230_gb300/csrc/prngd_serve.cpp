@@ -27,12 +27,14 @@
 
 #include "prngd.h"
 #include "prngd_internal.h"
+#include "prngd_pool.h"
 
 using prngd_host::fail;
 
 namespace {
 
-// First-fit allocator over one device allocation (offsets in bytes, 256-byte granules).
+// The output pool: one device allocation, its ranges handed out by a first-fit RangePool
+// (offsets in bytes, 256-byte granules, so every request's output is 256-byte aligned).
 class Pool {
  public:
   bool init(size_t bytes) {
@@ -40,52 +42,22 @@ class Pool {
       cudaGetLastError();
       return false;
     }
-    size_ = bytes;
-    free_[0] = bytes;
+    ranges_.reset(bytes);
     return true;
   }
   ~Pool() {
     if (base_) cudaFree(base_);
   }
   // returns offset or SIZE_MAX
-  size_t alloc(size_t bytes) {
-    bytes = (bytes + 255) & ~(size_t)255;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        const size_t off = it->first, len = it->second;
-        free_.erase(it);
-        if (len > bytes) free_[off + bytes] = len - bytes;
-        used_ += bytes;
-        return off;
-      }
-    }
-    return SIZE_MAX;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = (bytes + 255) & ~(size_t)255;
-    used_ -= bytes;
-    auto it = free_.emplace(off, bytes).first;
-    auto nx = std::next(it);
-    if (nx != free_.end() && it->first + it->second == nx->first) {
-      it->second += nx->second;
-      free_.erase(nx);
-    }
-    if (it != free_.begin()) {
-      auto pv = std::prev(it);
-      if (pv->first + pv->second == it->first) {
-        pv->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
+  size_t alloc(size_t bytes) { return ranges_.alloc(bytes); }
+  void release(size_t off, size_t bytes) { ranges_.release(off, bytes); }
   void* ptr(size_t off) const { return (char*)base_ + off; }
-  size_t used() const { return used_; }
-  size_t size() const { return size_; }
+  size_t used() const { return ranges_.used(); }
+  size_t size() const { return ranges_.size(); }
 
  private:
   void* base_ = nullptr;
-  size_t size_ = 0, used_ = 0;
-  std::map<size_t, size_t> free_;
+  prngd_host::RangePool ranges_;
 };
 
 struct Req {

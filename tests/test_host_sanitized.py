@@ -1,5 +1,5 @@
-"""The host-compiled checks (the library's __host__ __device__ arithmetic, its GF(2) jump code and
-MRG32k3a step, and the C oracle they are compared with) rebuilt with AddressSanitizer and
+"""The host-compiled checks (the library's __host__ __device__ arithmetic, its GF(2) jump code,
+MRG32k3a step and serving-pool allocator, and the C oracle they are compared with) rebuilt with AddressSanitizer and
 UndefinedBehaviorSanitizer, every finding fatal: no out-of-bounds access, no signed overflow, no
 shift past the word width on any path these checks reach."""
 import os
@@ -31,7 +31,8 @@ def _build(tmp_path, name, with_oracle):
     return exe
 
 
-@pytest.mark.parametrize("name,with_oracle", [("math_check", True), ("jump_check", False), ("mrg_check", True)])
+@pytest.mark.parametrize("name,with_oracle", [("math_check", True), ("jump_check", False), ("mrg_check", True),
+                                              ("pool_check", False)])
 def test_host_checks_under_sanitizers(tmp_path, name, with_oracle):
     exe = _build(tmp_path, name, with_oracle)
     env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0:abort_on_error=1", UBSAN_OPTIONS="print_stacktrace=1")
