@@ -204,8 +204,10 @@ int prng_fill_split(prng_t h, void* d_out, uint64_t per_stream, int form, int mo
  * At w = 32 under Eq. 4 (forms B and C) pair i is rounded by the route the fills use for output
  * i mod 4 of a row (integer normalisation or the u64 -> f64 conversion instruction); both give
  * the same bits.
- * d_u1, d_u2: device arrays of n uint32; d_out: device array of n 8-byte outputs.
- * Errors: PRNG_EINVAL (w outside [2, 32], unknown form or mode bits, null pointers), PRNG_ECUDA.
+ * d_u1, d_u2: device arrays of n uint32 (4-byte aligned); d_out: device array of n 8-byte
+ * outputs (8-byte aligned).
+ * Errors: PRNG_EINVAL (w outside [2, 32], unknown form or mode bits, null or misaligned
+ * pointers), PRNG_ECUDA.
  */
 int prng_convert_pairs(int w, int form, int mode, const uint32_t* d_u1, const uint32_t* d_u2, uint64_t n,
                        uint64_t* d_out, void* cuda_stream);
@@ -383,6 +385,12 @@ int prng_server_step(prng_server_t s);
 int prng_server_poll(prng_server_t s, uint64_t id, int* done, void** d_out);
 int prng_server_read(prng_server_t s, uint64_t id, void* host_dst, size_t bytes);
 int prng_server_release(prng_server_t s, uint64_t id);
+/* Withdraw a request that has not been launched yet: its pool memory is freed, its id is
+ * forgotten, and the client's streams do not advance (its later requests continue from the
+ * state the earlier ones left). A request already on the device, or finished, cannot be
+ * withdrawn: PRNG_EBUSY (wait for it, then release it). Errors: PRNG_EINVAL, PRNG_ENOTFOUND,
+ * PRNG_EBUSY. */
+int prng_server_cancel(prng_server_t s, uint64_t id);
 /* Step until nothing is waiting or running, at most timeout_s seconds (PRNG_ETIMEOUT). */
 int prng_server_drain(prng_server_t s, double timeout_s);
 int prng_server_info(prng_server_t s, uint64_t* n_clients, uint64_t* batches, uint64_t* completed,

@@ -79,6 +79,7 @@ _SIGNATURES = {
     "prng_server_poll": (_i32, [_P, _u64, ctypes.POINTER(_i32), ctypes.POINTER(_vp)]),
     "prng_server_read": (_i32, [_P, _u64, _vp, _sz]),
     "prng_server_release": (_i32, [_P, _u64]),
+    "prng_server_cancel": (_i32, [_P, _u64]),
     "prng_server_drain": (_i32, [_P, _dbl]),
     "prng_server_info": (_i32, [_P, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64),
                                 ctypes.POINTER(_u64), ctypes.POINTER(_sz)]),
@@ -295,6 +296,10 @@ def prng_server_read(s: int, rid: int, host) -> None:
 
 def prng_server_release(s: int, rid: int) -> None:
     _check(lib().prng_server_release(s, rid))
+
+
+def prng_server_cancel(s: int, rid: int) -> None:
+    _check(lib().prng_server_cancel(s, rid))
 
 
 def prng_server_drain(s: int, timeout_s: float = 60.0) -> None:

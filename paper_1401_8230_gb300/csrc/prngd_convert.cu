@@ -82,6 +82,8 @@ extern "C" int prng_convert_pairs(int w, int form, int mode, const uint32_t* d_u
   if (mode & ~kAllModes) return fail(PRNG_EINVAL, "unknown mode bits 0x%x", (unsigned)mode);
   if (n == 0) return PRNG_OK;
   if (!d_u1 || !d_u2 || !d_out) return fail(PRNG_EINVAL, "null pointer");
+  if (((uintptr_t)d_u1 & 3) || ((uintptr_t)d_u2 & 3) || ((uintptr_t)d_out & 7))
+    return fail(PRNG_EINVAL, "d_u1 and d_u2 must be 4-byte and d_out 8-byte aligned");
   prngd::FillParams p;
   memset(&p, 0, sizeof(p));
   p.dc = make_divconst(w);

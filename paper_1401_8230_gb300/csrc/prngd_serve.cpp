@@ -308,6 +308,28 @@ int prng_server_release(prng_server_t s, uint64_t id) {
   return PRNG_OK;
 }
 
+int prng_server_cancel(prng_server_t s, uint64_t id) {
+  if (!s) return fail(PRNG_EINVAL, "null server");
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return fail(PRNG_ENOTFOUND, "request %llu", (unsigned long long)id);
+  if (it->second.state != 0)
+    return fail(PRNG_EBUSY, "request %llu is on the device or finished: wait, then release", (unsigned long long)id);
+  const Req r = it->second;
+  for (auto& w : s->waiting) {
+    auto pos = std::find(w.begin(), w.end(), id);
+    if (pos != w.end()) w.erase(pos);
+  }
+  auto cq = s->client_q.find(r.client);
+  if (cq != s->client_q.end()) {
+    auto pos = std::find(cq->second.begin(), cq->second.end(), id);
+    if (pos != cq->second.end()) cq->second.erase(pos);
+    if (cq->second.empty()) s->client_q.erase(cq);
+  }
+  s->pool.release(r.off, r.bytes);
+  s->reqs.erase(it);
+  return PRNG_OK;
+}
+
 int prng_server_drain(prng_server_t s, double timeout_s) {
   if (!s) return fail(PRNG_EINVAL, "null server");
   const double t_end = s->now() + timeout_s;

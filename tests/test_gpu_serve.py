@@ -137,3 +137,36 @@ def test_admission_budget_and_trace_replay():
             assert P.prng_server_info(srv)["pool_used"] == 0
         finally:
             P.prng_server_destroy(srv)
+
+
+def test_cancel_withdraws_a_waiting_request():
+    """A cancelled request never runs: its pool memory returns at once and the client's next
+    request continues the streams as if it had never been submitted; a launched or finished
+    request cannot be cancelled, an unknown id is reported."""
+    seed, S, n_clients, min_per, w = 21, 32, 4, 16, 32
+    with P.Generator(seed, n_clients * S, w) as g:
+        srv = P.prng_server_create(g.h, S, min_per, 8 << 20)
+        try:
+            a = P.prng_server_submit(srv, 0, 3000, P.FORM_B_INTBITS)
+            b = P.prng_server_submit(srv, 0, 5000, P.FORM_A_FP64)  # waits behind a (same client)
+            used = P.prng_server_info(srv)["pool_used"]
+            P.prng_server_cancel(srv, b)
+            assert P.prng_server_info(srv)["pool_used"] == used - -(-5000 * 8 // 256) * 256  # whole 256-byte granules
+            c = P.prng_server_submit(srv, 0, 4000, P.FORM_C_F32PAIR)
+            P.prng_server_step(srv)
+            with pytest.raises(P.PrngError) as e:  # launched (or already finished)
+                P.prng_server_cancel(srv, a)
+            assert e.value.code == P.PRNG_EBUSY
+            with pytest.raises(P.PrngError) as e:
+                P.prng_server_cancel(srv, b)  # already withdrawn
+            assert e.value.code == P.PRNG_ENOTFOUND
+            P.prng_server_drain(srv, 30)
+            m = ClientModel(seed, 0, S, min_per, w)
+            assert same(read(srv, a, 3000, P.FORM_B_INTBITS), m.request(3000, P.FORM_B_INTBITS))
+            assert same(read(srv, c, 4000, P.FORM_C_F32PAIR), m.request(4000, P.FORM_C_F32PAIR))
+            P.prng_server_release(srv, a)
+            P.prng_server_release(srv, c)
+            assert P.prng_server_info(srv)["pool_used"] == 0
+            assert P.prng_server_info(srv)["completed"] == 2
+        finally:
+            P.prng_server_destroy(srv)
