@@ -39,3 +39,23 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+def build_c_caller(tmp_path):
+    """tests/host/abi_c_check.c linked against libprngd (include/prngd.h only) and the C oracle,
+    with gcc: a caller of the library that involves neither Python nor torch."""
+    import shutil
+    import subprocess
+
+    import paper_1401_8230_gb300 as P
+    from paper_1401_8230_gb300 import build as B
+
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("gcc not available")
+    P.lib()  # builds the library when it is missing or stale
+    exe = tmp_path / "abi_c_check"
+    subprocess.run([gcc, "-std=c11", "-O2", "-ffp-contract=off", "-Wall", "-I" + os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "host", "abi_c_check.c"), os.path.join(ROOT, "oracle", "prngd_oracle.c"),
+                    "-L" + B.LIB_DIR, "-lprngd", "-Wl,-rpath," + B.LIB_DIR, "-lm", "-o", str(exe)], check=True)
+    return exe

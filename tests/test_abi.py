@@ -57,3 +57,15 @@ def test_null_handle_is_rejected():
     assert ei.value.code == P.PRNG_EINVAL
     assert P.prng_state_bytes(0) == 0
     P.prng_destroy(0)  # no-op
+
+
+def test_c_caller_gets_argument_errors_without_python(tmp_path):
+    """A C program that includes only include/prngd.h and links libprngd: the argument errors
+    that need no GPU come back as PRNG_EINVAL with a message."""
+    import subprocess
+
+    from conftest import build_c_caller
+
+    exe = build_c_caller(tmp_path)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and "bad 0" in out.stdout, out.stdout
