@@ -268,6 +268,17 @@ int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist, uint64_t* 
                      uint64_t* d_rejects, void* cuda_stream);
 
 /*
+ * prng_stats_merge -- add one fused-statistics result into an accumulator, on the host:
+ * hist_in (65536 counts) and sums_in (S1..S4 as 128-bit (low, high) pairs, the layout
+ * prng_fused_stats leaves) into hist_acc and sums_acc of the same layout, each count and each
+ * 128-bit sum exactly (with the carry into the high word). Results of replicas that ran on
+ * disjoint stream ranges (one process per GPU) merge into the statistics of all their
+ * streams, in any order. All four pointers are host memory; no device work.
+ * Errors: PRNG_EINVAL (null pointer).
+ */
+int prng_stats_merge(const uint64_t* hist_in, const uint64_t* sums_in, uint64_t* hist_acc, uint64_t* sums_acc);
+
+/*
  * Batched requests. Many fill requests of uneven length run in one persistent launch over a
  * device work queue (a counter over items of 32 rows), replayed from a CUDA graph captured
  * once per launch shape. Each request's output is a stream-major block of rows, row j being

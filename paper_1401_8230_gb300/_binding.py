@@ -63,6 +63,7 @@ _SIGNATURES = {
     "prng_fill_f64_host": (_i32, [_P, _vp, _u64, _i32, _vp]),
     "prng_fill_f64_host_noalloc": (_i32, [_P, _vp, _u64, _i32, _vp, _vp]),
     "prng_fused_stats": (_i32, [_P, _u64, _vp, _vp, _vp, _vp]),
+    "prng_stats_merge": (_i32, [_vp, _vp, _vp, _vp]),
     "prng_state_bytes": (_sz, [_P]),
     "prng_submit": (_i32, [_P, ctypes.c_void_p, _i32, ctypes.POINTER(_u64), _vp]),
     "prng_poll": (_i32, [_P, _u64, ctypes.POINTER(_i32)]),
@@ -218,6 +219,12 @@ def prng_fill_f64_host_noalloc(h: int, out, per_stream: int, form: int = FORM_B_
 
 def prng_fused_stats(h: int, per_stream: int, hist, sums, rejects=None, stream=None) -> None:
     _check(lib().prng_fused_stats(h, per_stream, _ptr(hist), _ptr(sums), _ptr(rejects), _stream(stream)))
+
+
+def prng_stats_merge(hist_in, sums_in, hist_acc, sums_acc) -> None:
+    """Add one fused-statistics result (host arrays of uint64: 65536 counts, 8 sum words) into
+    an accumulator of the same layout."""
+    _check(lib().prng_stats_merge(_ptr(hist_in), _ptr(sums_in), _ptr(hist_acc), _ptr(sums_acc)))
 
 
 def prng_submit(h: int, reqs, stream=None) -> int:

@@ -13,6 +13,7 @@
 #include "prngd.h"
 #include "prngd_fill.cuh"
 #include "prngd_internal.h"
+#include "prngd_launch.h"
 
 using prngd::DivConst;
 using prngd::FillParams;
@@ -106,18 +107,19 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Looked up once per process (the driver entry point is the same for every device); the
+// initialisation of a function-local static is thread-safe.
 static EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
+  static const EncodeTiledFn fn = []() -> EncodeTiledFn {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = (EncodeTiledFn)p;
-  }
+      return (EncodeTiledFn)p;
+    cudaGetLastError();
+    return nullptr;
+  }();
   return fn;
 }
 
@@ -149,12 +151,9 @@ static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cu
   const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (map) {
     auto k = prngd::fill_tma_kernel<W, FORM, kNbuf, MAP>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
+    if (e != cudaSuccess) return e;
     k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
   } else {
     prngd::fill_plain_kernel<W, FORM, MAP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(p);

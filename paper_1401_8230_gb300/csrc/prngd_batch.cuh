@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "prngd_fill.cuh"
+#include "prngd_launch.h"
 
 namespace prngd {
 
@@ -373,12 +374,9 @@ template <int W, int FORM_ALL>
 cudaError_t launch_batch_kernel(const BatchParams& p, int warps, unsigned blocks, int max_req, cudaStream_t s) {
   auto k = batch_kernel<W, FORM_ALL>;
   const size_t smem = 1024 + (size_t)warps * kTileBytes + 4 * ((size_t)max_req + 1);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = prngd::smem_limit_once(k, 64 * 1024, attr);
+  if (e != cudaSuccess) return e;
   k<<<blocks, warps * 32, smem, s>>>(p);
   return cudaGetLastError();
 }

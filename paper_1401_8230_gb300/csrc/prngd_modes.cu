@@ -7,6 +7,7 @@
 
 #include "prngd_fill.cuh"
 #include "prngd_internal.h"
+#include "prngd_launch.h"
 
 namespace prngd_host {
 namespace {
@@ -19,12 +20,9 @@ cudaError_t launch_generic(const prngd::FillParams& p, const CUtensorMap* tmap, 
   const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (tmap) {
     auto k = prngd::fill_tma_kernel<0, FORM, 1, MAP>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
+    if (e != cudaSuccess) return e;
     k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *tmap);
   } else {
     prngd::fill_plain_kernel<0, FORM, MAP><<<blocks, kWarpsPerBlock * 32, 0, s>>>(p);

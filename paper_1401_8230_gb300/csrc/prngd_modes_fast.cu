@@ -6,6 +6,7 @@
 
 #include "prngd_fill.cuh"
 #include "prngd_internal.h"
+#include "prngd_launch.h"
 
 namespace prngd_host {
 namespace {
@@ -17,12 +18,9 @@ cudaError_t launch_fast(const prngd::FillParams& p, const CUtensorMap* tmap, cud
   const uint64_t warps = (p.n_streams + 31) / 32;
   const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   auto k = prngd::fill_tma_kernel<W, FORM, 1, MAP>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
+  if (e != cudaSuccess) return e;
   k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *tmap);
   return cudaGetLastError();
 }

@@ -18,6 +18,7 @@
 
 #include "prngd_fill.cuh"
 #include "prngd_internal.h"
+#include "prngd_launch.h"
 #include "prngd_mrg.cuh"
 
 namespace prngd {
@@ -155,12 +156,9 @@ cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, 
   const unsigned blocks = (unsigned)((p.n_streams + 255) / 256);
   if (map) {
     auto k = prngd::fill_mrg_tma_kernel<FORM, MAP>;
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
+    if (e != cudaSuccess) return e;
     k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
   } else {
     prngd::fill_mrg_plain_kernel<FORM, MAP><<<blocks, 256, 0, s>>>(p);

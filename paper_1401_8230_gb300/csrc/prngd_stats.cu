@@ -4,6 +4,7 @@
 
 #include "prngd.h"
 #include "prngd_internal.h"
+#include "prngd_launch.h"
 #include "prngd_stats.cuh"
 
 namespace prngd_host {
@@ -26,12 +27,9 @@ uint32_t stats_block_size(uint64_t n_streams, int num_sms) {
 template <int W>
 static cudaError_t launch_stats_w(const prngd::StatsParams& p, int num_sms, cudaStream_t s) {
   auto k = prngd::stats_kernel<W>;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStatsSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  static std::atomic<uint64_t> attr{0};
+  const cudaError_t e = prngd::smem_limit_once(k, (int)kStatsSmem, attr);
+  if (e != cudaSuccess) return e;
   const uint64_t units = (p.n_streams + p.unit - 1) / p.unit;
   const unsigned grid = (unsigned)(units < (uint64_t)num_sms ? units : (uint64_t)num_sms);
   k<<<grid, p.unit, kStatsSmem, s>>>(p);
@@ -64,6 +62,18 @@ int launch_stats(prng_ctx* h, uint64_t per_stream, uint64_t* d_hist, uint64_t* d
 }  // namespace prngd_host
 
 using namespace prngd_host;
+
+extern "C" int prng_stats_merge(const uint64_t* hist_in, const uint64_t* sums_in, uint64_t* hist_acc,
+                                uint64_t* sums_acc) {
+  if (!hist_in || !sums_in || !hist_acc || !sums_acc) return fail(PRNG_EINVAL, "null pointer");
+  for (int i = 0; i < 2 * prngd::kHistWords; ++i) hist_acc[i] += hist_in[i];
+  for (int p = 0; p < 4; ++p) {
+    const uint64_t lo = sums_acc[2 * p] + sums_in[2 * p];
+    sums_acc[2 * p + 1] += sums_in[2 * p + 1] + (lo < sums_in[2 * p] ? 1u : 0u);
+    sums_acc[2 * p] = lo;
+  }
+  return PRNG_OK;
+}
 
 extern "C" int prng_fused_stats(prng_t h, uint64_t per_stream, uint64_t* d_hist, uint64_t* d_sums,
                                 uint64_t* d_rejects, void* cuda_stream) {

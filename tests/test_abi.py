@@ -69,3 +69,30 @@ def test_c_caller_gets_argument_errors_without_python(tmp_path):
     exe = build_c_caller(tmp_path)
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert out.returncode == 0 and "bad 0" in out.stdout, out.stdout
+
+
+def test_stats_merge_is_exact_128_bit_addition():
+    """prng_stats_merge (host only) against Python integers: counts add, and each 128-bit sum
+    carries from its low word into its high word."""
+    import numpy as np
+
+    rng = np.random.default_rng(8)
+    acc_h = np.zeros(65536, dtype=np.uint64)
+    acc_s = np.zeros(8, dtype=np.uint64)
+    want_h = np.zeros(65536, dtype=object)
+    want_s = [0] * 4
+    for k in range(6):
+        h = rng.integers(0, 2**40, 65536, dtype=np.uint64)
+        lo = rng.integers(2**63, 2**64 - 1, 4, dtype=np.uint64, endpoint=True)  # large low words: carries
+        hi = rng.integers(0, 2**20, 4, dtype=np.uint64)
+        s = np.empty(8, dtype=np.uint64)
+        s[0::2], s[1::2] = lo, hi
+        P.prng_stats_merge(h, s, acc_h, acc_s)
+        want_h += h.astype(object)
+        for p in range(4):
+            want_s[p] += int(lo[p]) + (int(hi[p]) << 64)
+    assert [int(v) for v in acc_h] == [int(v) for v in want_h]
+    assert [int(acc_s[2 * p]) + (int(acc_s[2 * p + 1]) << 64) for p in range(4)] == want_s
+    with pytest.raises(P.PrngError) as ei:
+        P.prng_stats_merge(None, acc_s, acc_h, acc_s)
+    assert ei.value.code == P.PRNG_EINVAL
