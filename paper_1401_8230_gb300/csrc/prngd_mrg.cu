@@ -53,12 +53,16 @@ __global__ void mrg_seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
 // kMapCvt (PRNG_MODE_BALANCED, form B's rounding route).
 template <int FORM, int MAP = 0>
 __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, const FillParams& p) {
-  uint32_t u1, u2;
-  for (;;) {
-    u1 = mrg_next(g) - 1u;
-    u2 = mrg_next(g) - 1u;
-    if (u1 - 1u < kMrgM1 - 2u) break;  // u1 not in {0, M - 1}
-    ++rej;
+  // the usual case, an accepted pair, is straight-line code (no loop around the state's
+  // rotation); a rejected pair (u1 in {0, M - 1}, probability 2/M) takes the next pair
+  uint32_t u1 = mrg_next(g) - 1u;
+  uint32_t u2 = mrg_next(g) - 1u;
+  if (__builtin_expect(u1 - 1u >= kMrgM1 - 2u, 0)) {
+    do {
+      ++rej;
+      u1 = mrg_next(g) - 1u;
+      u2 = mrg_next(g) - 1u;
+    } while (u1 - 1u >= kMrgM1 - 2u);
   }
   const uint64_t n = (uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u);
   // form A: the conversion instruction, then the scale (its definition's two FP64 steps)

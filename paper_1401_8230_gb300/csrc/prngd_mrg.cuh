@@ -28,7 +28,7 @@ PRNGD_HD uint32_t mod_m1(uint64_t v) {
 // high word (< 32) folds with a 32-bit multiply; a carry out of that add (the sum then < 2^20)
 // folds once more.
 PRNGD_HD uint32_t mod_m2(uint64_t v) {
-  const uint64_t w = (v >> 32) * 22853u + (v & 0xFFFFFFFFull);
+  const uint64_t w = (uint64_t)(uint32_t)(v >> 32) * 22853u + (uint32_t)v;  // one 32 x 32 -> 64 multiply-add
   const uint32_t t = (uint32_t)(w >> 32) * 22853u;  // < 2^20
   uint32_t r = (uint32_t)w + t;
   if (r < t) r += 22853u;
@@ -58,10 +58,11 @@ PRNGD_HD uint32_t mrg_next(Mrg32k3a& g) {
 // n + E0 + (S >> 32) unless the low word of S lies within 16 of 2^32 (`ok` = 0). For A >= 2^22
 // it is at least 2^54, and it rounds like the xorshift fast path's I.
 PRNGD_HD uint64_t mrg_fast_I(uint64_t n, uint32_t& ok) {
-  const uint64_t nh = n >> 32, nl = n & 0xFFFFFFFFull;
-  const uint64_t E0 = 420u * nh;
-  const uint64_t E1 = 420u * nl + 132300u * nh;
-  const uint64_t E2 = 132300u * nl + 37044000u * nh;
+  // the halves as 32-bit values, so that every product is one 32 x 32 -> 64 multiply(-add)
+  const uint32_t nh = (uint32_t)(n >> 32), nl = (uint32_t)n;
+  const uint64_t E0 = (uint64_t)nh * 420u;
+  const uint64_t E1 = (uint64_t)nl * 420u + (uint64_t)nh * 132300u;
+  const uint64_t E2 = (uint64_t)nl * 132300u + (uint64_t)nh * 37044000u;
   const uint64_t S = E1 + (E2 >> 32);
   ok = ((uint32_t)S < 0xFFFFFFF0u) ? 1u : 0u;
   return n + E0 + (S >> 32);
