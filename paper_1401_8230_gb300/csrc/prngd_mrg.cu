@@ -72,8 +72,8 @@ __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, 
   if (__builtin_expect(u1 > (1u << 22), 1)) {  // A >= 2^22: the series fast path
     const uint64_t I = mrg_fast_I(n, ok);
     // the fills' rounding routes (cvt_group_mask): form C by the conversion instruction; form B
-    // by integer operations, or by the conversion under PRNG_MODE_BALANCED (measured 206 and
-    // 216 Gsamples/s; form C 198)
+    // by integer operations, or by the conversion under PRNG_MODE_BALANCED (measured 216 and
+    // 224 Gsamples/s)
     bits = cvt_group_mask<FORM, 32, MAP>() ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
   }
   if (__builtin_expect(!ok, 0)) bits = rn_bits_exact(n, p.dc);  // small values, margin cases
