@@ -96,3 +96,20 @@ def test_stats_merge_is_exact_128_bit_addition():
     with pytest.raises(P.PrngError) as ei:
         P.prng_stats_merge(None, acc_s, acc_h, acc_s)
     assert ei.value.code == P.PRNG_EINVAL
+
+
+def test_binding_mirrors_every_declaration():
+    """Every function include/prngd.h declares has a ctypes signature in the binding with the
+    same number of parameters, and a Python function of the same name."""
+    from paper_1401_8230_gb300 import _binding as B
+
+    text = open(os.path.join(ROOT, "include", "prngd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    decls = dict(re.findall(r"\b(prng_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.S))
+    assert set(decls) == set(declared_functions())
+    for name, params in decls.items():
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert name in B._SIGNATURES, name
+        assert len(B._SIGNATURES[name][1]) == n, (name, n, len(B._SIGNATURES[name][1]))
+        assert callable(getattr(B, name, None)), name
