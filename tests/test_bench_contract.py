@@ -46,3 +46,28 @@ def test_reference_arm_under_torchrun_prints_from_rank_0_only():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2
+
+
+def test_clock_sampler_child_never_outlives_the_bench(monkeypatch, tmp_path):
+    """The clock sampler's child process (nvidia-smi on a GPU machine; a stand-in here) is ended by
+    stop(), and by the exit handler start() registers if stop() is never reached."""
+    import atexit
+
+    import bench
+
+    real_popen = subprocess.Popen
+    monkeypatch.setattr(bench.subprocess, "Popen",
+                        lambda args, **kw: real_popen(["sleep", "60"], **kw))
+    monkeypatch.setenv("PRNGD_CLOCKS_DIR", str(tmp_path))
+    registered = []
+    monkeypatch.setattr(atexit, "register", lambda f: registered.append(f))
+    monkeypatch.setattr(atexit, "unregister", lambda f: None)
+    a = bench.ClockSampler(0)
+    a.start()
+    assert a.proc.poll() is None and len(registered) == 1
+    registered[0]()  # what interpreter exit would run after an exception in the timed region
+    assert a.proc.poll() is not None
+    b = bench.ClockSampler(0)
+    b.start()
+    res = b.stop()
+    assert b.proc.poll() is not None and res["samples"] == 0
