@@ -1,20 +1,22 @@
 """Pins for the oracle's MRG32k3a base generator and the method over its draws (Demchik and
 Gulov, Section 2: the base generator should be one with good statistics, e.g. MRG32k3a).
 
-The recurrence constants are pinned by number theory (partly: see below): each component's characteristic
-polynomial must be primitive modulo its prime, i.e. z has multiplicative order m^3 - 1 in
-GF(m)[z]/(P) (checked with the prime factors of m^3 - 1 from sympy) -- the property that gives
-the generator its period. A mistyped constant breaks it only with probability ~0.6 (primitive
-cubics are common), and no published known-answer vector is used, so the constants are
-partially pinned; the method over the draws is fully pinned. The oracle's stepping,
-combination and seeding are checked against those constants and the pinned splitmix64; the
-method's reduction with M = m1 grid points against Eq. (4) in exact rationals."""
+The two recurrences are pinned by published values: the oracle's one-step transition
+matrices, recovered by stepping it from unit states, raised to the powers 2^76 and 2^127
+must equal the four jump matrices published with L'Ecuyer et al.'s RngStreams package
+(tests/golden/mrg32k3a_jump_matrices.txt). Any mistyped multiplier, sign, modulus or state
+order changes those powers. The combination z = (x1 - x2) mod m1 (0 reported as m1) is
+pinned by states whose other component is zero, so that z reduces to one component whose
+values the matrices pin. Each component's characteristic polynomial is also checked to be
+primitive (the property that gives the period). Seeding uses the pinned splitmix64, and the
+method's reduction with M = m1 grid points is checked against Eq. (4) in exact rationals."""
 from fractions import Fraction
 
 import numpy as np
 import pytest
 
 import oracle as O
+from conftest import read_golden
 
 M1, M2 = O.MRG_M1, O.MRG_M2
 # x1_n = A12 x1_{n-2} - A13N x1_{n-3} (mod m1), x2_n = A21 x2_{n-1} - A23N x2_{n-3} (mod m2)
@@ -116,3 +118,80 @@ def test_mrg_outputs_look_uniform():
     out, _ = O.fill_mrg(11, 0, 64, 2000, O.FORM_B)
     assert abs(out.mean() - 0.5) < 0.01 and abs(out.var() - 1 / 12) < 0.005
     assert out.min() > 0.0 and out.max() < 1.0
+
+
+def _matmul(A, B, m):
+    return [[sum(A[i][k] * B[k][j] for k in range(3)) % m for j in range(3)] for i in range(3)]
+
+
+def _oracle_transition(component):
+    """The oracle's one-step matrix of a component, column j = the state after one step from
+    the unit state e_j (the other component held at a fixed nonzero state)."""
+    cols = []
+    for j in range(3):
+        st = np.array([5, 6, 7, 5, 6, 7], dtype=np.uint32)
+        base = 0 if component == 1 else 3
+        st[base:base + 3] = 0
+        st[base + j] = 1
+        _, after = O.mrg_outputs(st, 1)
+        cols.append([int(v) for v in after[base:base + 3]])
+    return [[cols[j][i] for j in range(3)] for i in range(3)]
+
+
+@pytest.mark.parametrize("component", [1, 2])
+def test_transition_powers_equal_published_jump_matrices(component):
+    golden = {r[0]: [int(v) for v in r[1:]] for r in read_golden("mrg32k3a_jump_matrices.txt")}
+    m = M1 if component == 1 else M2
+    A = _oracle_transition(component)
+    P = A
+    for e in range(1, 128):
+        P = _matmul(P, P, m)  # A^(2^e)
+        if e in (76, 127):
+            flat = golden[f"A{component}p{e}"]
+            assert P == [flat[0:3], flat[3:6], flat[6:9]], (component, e)
+
+
+def test_transition_matrix_is_the_stepping():
+    """The recovered matrix, applied 1000 times, gives the oracle's own state after 1000 steps
+    from a seeded state (the pinned matrix is the generator the fills use)."""
+    st = O.mrg_stream_seed(5, 77)
+    _, after = O.mrg_outputs(st, 1000)
+    for comp, m, base in [(1, M1, 0), (2, M2, 3)]:
+        A = _oracle_transition(comp)
+        x = [int(v) for v in st[base:base + 3]]
+        for _ in range(1000):
+            x = [sum(A[i][k] * x[k] for k in range(3)) % m for i in range(3)]
+        assert x == [int(v) for v in after[base:base + 3]]
+
+
+def test_combination_reduces_to_one_component():
+    """With x2 = 0 the output is x1 (0 reported as m1); with x1 = 0 it is m1 - x2 (x2 = 0
+    reported as m1): z = (x1 - x2) mod m1 in [1, m1], term by term."""
+    st = O.mrg_stream_seed(12, 3)
+    only1 = st.copy()
+    only1[3:] = 0
+    z, after = O.mrg_outputs(only1, 500)
+    A1 = _oracle_transition(1)
+    x = [int(v) for v in only1[:3]]
+    for n in range(500):
+        x = [sum(A1[i][k] * x[k] for k in range(3)) % M1 for i in range(3)]
+        assert int(z[n]) == (x[2] if x[2] else M1)
+    assert list(after[3:]) == [0, 0, 0]
+    only2 = st.copy()
+    only2[:3] = 0
+    z, _ = O.mrg_outputs(only2, 500)
+    A2 = _oracle_transition(2)
+    x = [int(v) for v in only2[3:]]
+    for n in range(500):
+        x = [sum(A2[i][k] * x[k] for k in range(3)) % M2 for i in range(3)]
+        assert int(z[n]) == (M1 - x[2] if x[2] else M1)
+
+
+def test_equal_components_report_m1():
+    """x1_n = x2_n gives z = 0, which the generator reports as m1. Built from unit-like states:
+    x1 state (0, 1, 0) steps to A12; x2 state (0, 0, c) steps to A21 c, with c = A12 / A21 mod m2."""
+    c = A12 * pow(A21, -1, M2) % M2
+    st = np.array([0, 1, 0, 0, 0, c], dtype=np.uint32)
+    z, after = O.mrg_outputs(st, 1)
+    assert int(after[2]) == A12 and int(after[5]) == A12
+    assert int(z[0]) == M1
