@@ -85,17 +85,15 @@ __device__ __forceinline__ void add_u128_global(uint64_t* lohi, uint64_t lo, uin
 // Persistent kernel: block b processes work units b, b + gridDim.x, ...; unit u is streams
 // [u*T, (u+1)*T) with T = blockDim.x, one stream per thread. The histogram lives in shared
 // memory as 16-bit counters; a counter is at most 2^15 at the start of an interval (an
-// increment that returns a half >= 2^15 raises the flush flag, checked at the interval's
-// barrier) and gains at most T * kStatsInterval <= 32767 within it, so it never wraps.
+// increment that returns a half >= 2^15 asks for a flush, decided by the OR over the block
+// at the interval's barrier) and gains at most T * kStatsInterval <= 32767 within it, so it never wraps.
 template <int W>
 __global__ void __launch_bounds__(1024, 1) stats_kernel(const StatsParams p) {
   extern __shared__ uint32_t hist[];
   __shared__ unsigned long long s_sum[8];
-  __shared__ int s_flag;
   const uint32_t T = blockDim.x;
   for (uint32_t i = threadIdx.x; i < kHistWords; i += T) hist[i] = 0;
   if (threadIdx.x < 8) s_sum[threadIdx.x] = 0;
-  if (threadIdx.x == 0) s_flag = 0;
   __syncthreads();
 
   const uint64_t n_units = (p.n_streams + p.unit - 1) / p.unit;
@@ -129,18 +127,16 @@ __global__ void __launch_bounds__(1024, 1) stats_kernel(const StatsParams p) {
         }
       }
       since_fold += cnt;
-      if (ovf & 0x80008000u) s_flag = 1;
-      __syncthreads();
-      if (s_flag) {  // uniform: every thread read the flag after the barrier
-        __syncthreads();
+      // The barrier's OR gives every thread the same answer, so the flush branch (and the
+      // barrier inside it) is taken by the whole block or by none of it.
+      if (__syncthreads_or((ovf & 0x80008000u) != 0u)) {
         for (uint32_t i = threadIdx.x; i < kHistWords; i += T) {
           const uint32_t v = hist[i];
           hist[i] = 0;
           if (v & 0xFFFFu) atomicAdd((unsigned long long*)&p.hist[i], (unsigned long long)(v & 0xFFFFu));
           if (v >> 16) atomicAdd((unsigned long long*)&p.hist[i + 32768], (unsigned long long)(v >> 16));
         }
-        if (threadIdx.x == 0) s_flag = 0;
-        __syncthreads();
+        __syncthreads();  // the next interval's increments start on the zeroed counters
       }
       if (since_fold >= (1ull << 24)) {  // per-thread 64-bit sums hold < 2^24 terms of < 2^32
         add_u128_shared(&s_sum[0], &s_sum[1], a1);

@@ -93,3 +93,35 @@ def test_stats_full_size_properties():
         _, r, st_want = O.fill_state(O.stream_seed(seed, int(sidx)), per, w, O.FORM_N)
         assert np.array_equal(st[sidx], st_want)
         assert rej[sidx] == r
+
+
+def _stats_block(ns, sms):
+    """Block size the library picks for ns streams: whole rounds of one block per SM, a
+    multiple of 32, at most 992 (so T * 32 outputs per interval stay below 2^15)."""
+    per_round = sms * 992
+    rounds = -(-ns // per_round)
+    t = -(-ns // (sms * rounds))
+    return min(max(-(-t // 32) * 32, 32), 992)
+
+
+@pytest.mark.parametrize("w,ns,per", [
+    (2, 992, 2**15 + 77),      # 32-thread blocks, 8 bins: every block passes 2^16 in some bin
+    (3, 992, 3 * 2**15 + 5),   # 48 bins
+    (4, 32, 2**20 + 3),        # one block of one warp, 224 bins
+    (2, 152 * 992, 1000),      # 992-thread blocks (31 warps share the counters), ragged last interval
+])
+def test_stats_counter_flush(w, ns, per):
+    """Few bins and many outputs per block, so the 16-bit shared counters reach 2^15 again and
+    again and the block must flush them to the global histogram mid-run. Histogram, the four
+    128-bit sums and the reject counts must equal the oracle's exactly."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    T = _stats_block(ns, sms)
+    bins = (1 << w) ** 2 - 2 * (1 << w)  # accepted outputs at w are the D - 1 grid points
+    assert min(T, ns) * per // bins > 2**16, "the case must overflow a 16-bit counter"
+    seed = 900 + w
+    with P.Generator(seed, ns, w) as g:
+        hist, sums, rej = gpu_stats(g, per)
+    want_h, want_s, want_r = O.stats(seed, 0, ns, per, w)
+    assert np.array_equal(rej, want_r)
+    assert np.array_equal(hist, want_h)
+    assert sums == want_s
