@@ -76,6 +76,8 @@ def workload_desc():
     return {"workload": name,
             "n_streams": N_STREAMS, "per_stream": PER_STREAM, "w": W, "form": "B", "mode": "PRNG_MODE_BALANCED",
             "output": "f64",
+            "arithmetic": "32/64-bit integer draws, accept-reject, n and rounding; the u64->f64 conversion "
+                          "instruction rounds 3 of 4 outputs (the same bits)",
             "l2": f"{N_STREAMS * PER_STREAM * 8 / 2**30:.2f} GiB output per step > 129 MB L2: no flush"}
 
 
@@ -228,7 +230,7 @@ def run_reference(args):
     value = total / sum(times) / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {**workload_desc(), "sample": f"{n} streams x 1024 per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"streams 0..{n - 1} of the bulk workload per step"},
@@ -335,7 +337,7 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {**workload_desc(), "parallelism": f"replicas x{world} (disjoint stream ranges)"},
             "roofline": roofline, "clocks": clk, "gpu_launches": args.steps}
 
@@ -450,6 +452,54 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
             "frac": rate * alu / ALU_PEAK_GOPS, "alu_ops_per_output": alu,
             "peak_kind": "ALU pipe: 64 lanes per clock per SM x 152 SMs x 2.07 GHz (ncu peak_sustained, max clock)"}
     gs.close()
+    res["precision"] = precision(torch, P)
+    return res
+
+
+def precision(torch, P):
+    """Steps (differences of the bit patterns) of forms A and C from form B's correctly rounded
+    double, over every output of the bulk workload: fresh handles, so each form rounds the
+    same draws. Form B is RN(n/D) (the GPU tests compare it with the oracle's exact division);
+    its balanced route is compared with the integer-only one here. Bounds in ulp(n/D): form A
+    < 1.5 (1 step), B < 0.5 (0), C < 8.5 (8)."""
+    n = N_STREAMS * PER_STREAM
+
+    def fill(form, mode=0):
+        out = torch.empty(n, dtype=torch.float64, device="cuda")
+        gg = P.Generator(SEED, N_STREAMS, W)
+        gg.fill_mode(out, PER_STREAM, form, mode)
+        torch.cuda.synchronize()
+        gg.close()
+        return out
+
+    b = fill(P.FORM_B_INTBITS).view(torch.int64)
+    res = {}
+    for name, form, mode, bound, steps_bound in [
+            ("formA_fp64", P.FORM_A_FP64, 0, 1.5, 1), ("formB_balanced", P.FORM_B_INTBITS, P.MODE_BALANCED, 0.5, 0),
+            ("formC_f32pair", P.FORM_C_F32PAIR, 0, 8.5, 8)]:
+        x = fill(form, mode)
+        worst, at_worst = 0, 0
+        for lo in range(0, n, 1 << 27):
+            hi_ = min(n, lo + (1 << 27))
+            if form == P.FORM_C_F32PAIR:
+                pair = x[lo:hi_].view(torch.float32).view(-1, 2).to(torch.float64)
+                xi = (pair[:, 0] + pair[:, 1]).view(torch.int64)  # exact: at most 48 significant bits
+            else:
+                xi = x[lo:hi_].view(torch.int64)
+            d = (xi - b[lo:hi_]).abs()
+            m = int(d.max())
+            if m > worst:
+                worst, at_worst = m, 0
+            if m == worst:
+                at_worst += int((d == worst).sum())
+        del x
+        res[name] = {"max_ulp_vs_rn": worst, "share_at_max": at_worst / n, "outputs": n,
+                     "bound_steps_from_rn": steps_bound, "bound_err_ulp_vs_exact": bound}
+    res["formB_intbits"] = {"max_ulp_vs_rn": 0, "bound_steps_from_rn": 0, "bound_err_ulp_vs_exact": 0.5,
+                            "note": "the reference of the steps above; equal to the oracle's exact RN(n/D) in "
+                                    "the GPU tests"}
+    del b
+    torch.cuda.empty_cache()
     return res
 
 

@@ -55,7 +55,8 @@ extern "C" {
 #define PRNG_FORM_B_INTBITS 1 /* double RN(n/D), correctly rounded, built with integer ops  */
                               /* only (see PRNG_MODE_BALANCED)                          */
 #define PRNG_FORM_C_F32PAIR 2 /* two floats (hi, lo): hi = RN32(d), lo = RN32(d - hi), with */
-                              /* d the form-B value; stored interleaved hi, lo               */
+                              /* d the form-B value; stored interleaved hi, lo; the exact    */
+                              /* sum hi + lo is within 8.5 ulp64 of n/D (prng_fill_f32pair)  */
 #define PRNG_FORM_L_ALGO1 4   /* double: Algorithm 1's Z evaluated literally in FP64, one IEEE */
                               /* operation at a time (prng_fill_mode only)                    */
 
@@ -136,6 +137,11 @@ int prng_fill_f64(prng_t h, double* d_out, uint64_t per_stream, int form, uint64
  * prng_fill_f32pair -- as prng_fill_f64 with form C: d_out holds 2 * n_streams * per_stream
  * floats, element 2*(s*per_stream+i) = hi and 2*(s*per_stream+i)+1 = lo of output i of
  * stream s, with hi = RN32(d), lo = RN32(d - hi) and d = RN(n/D).
+ * Error bound: |hi + lo - n/D| < 8.5 ulp(n/D), ulp(V) = 2^(floor(log2 V) - 52). d is within
+ * half an ulp of n/D. If |d - hi| is half an FP32 ulp of d it is a power of two and lo is
+ * exact; otherwise |d - hi| lies a binade lower, where an FP32 ulp is 16 FP64 ulps, so lo's
+ * rounding adds at most 8. hi + lo (at most 48 significant bits) is a double at most 8
+ * steps from d. Measured on 2^30 outputs at w = 32: 8 steps, error up to 8.4999 ulp.
  */
 int prng_fill_f32pair(prng_t h, float* d_out, uint64_t per_stream, uint64_t* d_rejects,
                       void* cuda_stream);
@@ -237,7 +243,12 @@ int prng_fill_f64_host(prng_t h, double* host_out, uint64_t per_stream, int form
  * 8 * PRNG_NOALLOC_MAX_SLICE_STREAMS bytes (17 MiB); every GPU that loads the library holds
  * it until the process exits.
  * Work runs on `cuda_stream` (NULL = legacy default stream) in slices that fit the array,
- * one after another; the call synchronises that stream before returning. The first call on a
+ * one after another; the call synchronises that stream before returning. It orders itself
+ * after nothing else: earlier asynchronous work on this handle queued on another stream
+ * (a prng_fill_* or prng_fused_stats that is still running) must be complete or ordered
+ * before `cuda_stream` by the caller (an event wait, or a synchronise), or this call reads
+ * stream states that are still being updated. prng_fill_f64_host needs no such care: it
+ * synchronises the device first. The first call on a
  * device looks up the array's device address (once per device); make that first call
  * before any stream capture.
  * All calls share the one array, and it keeps the last call's contents. Calls that overlap

@@ -59,3 +59,16 @@ def build_c_caller(tmp_path):
                     os.path.join(ROOT, "tests", "host", "abi_c_check.c"), os.path.join(ROOT, "oracle", "prngd_oracle.c"),
                     "-L" + B.LIB_DIR, "-lprngd", "-Wl,-rpath," + B.LIB_DIR, "-lm", "-o", str(exe)], check=True)
     return exe
+
+
+def ulp_error(x, n, D):
+    """|x - n/D| in units of ulp(n/D) = 2^(floor(log2(n/D)) - 52), exactly, as a Fraction.
+    x is a float or a Fraction (e.g. hi + lo of a float pair); 0 < n < D."""
+    from fractions import Fraction
+
+    e = n.bit_length() - D.bit_length()  # 2^e <= n/D < 2^(e+1) after the adjustment below
+    if (n << max(0, -e)) < (D << max(0, e)):
+        e -= 1
+    ulp = Fraction(2) ** (e - 52)
+    return abs(Fraction(x) - Fraction(n, D)) / ulp
+
