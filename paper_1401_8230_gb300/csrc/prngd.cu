@@ -124,20 +124,30 @@ static EncodeTiledFn encode_fn() {
 }
 
 // 2D map over a stream-major array of 8-byte outputs: dim0 = outputs per stream (contiguous),
-// dim1 = streams; box = 16 outputs x 32 streams with the 128-byte swizzle.
-bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream) {
+// dim1 = streams; box = box_x outputs x box_y streams, rows of box_x * 8 bytes swizzled in
+// 128-byte (box_x = 16) or 64-byte (box_x = 8) mode.
+// pitch: bytes from one stream's row to the next (0: per_stream * 8).
+bool encode_out_map_box(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream, uint32_t box_x,
+                        uint32_t box_y, uint64_t pitch) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn) return false;
-  if (((uintptr_t)out & 15) || (per_stream & 1) || per_stream >= (1ull << 31) || n_streams >= (1ull << 31))
+  if (!pitch) pitch = per_stream * 8;
+  if (!fn || (box_x != 16 && box_x != 8) || box_y == 0 || box_y > 256) return false;
+  if (((uintptr_t)out & 15) || (per_stream & 1) || per_stream == 0 || per_stream >= (1ull << 31) ||
+      n_streams >= (1ull << 31) || (pitch & 15) || pitch < per_stream * 8)
     return false;
   cuuint64_t gdim[2] = {per_stream, n_streams};
-  cuuint64_t gstride[1] = {per_stream * 8};
-  cuuint32_t box[2] = {(cuuint32_t)prngd::kChunk, 32};
+  cuuint64_t gstride[1] = {pitch};
+  cuuint32_t box[2] = {box_x, box_y};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, out, gdim, gstride, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, box_x == 16 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+// The fills' map: box = 16 outputs x 32 streams with the 128-byte swizzle.
+bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream) {
+  return encode_out_map_box(map, out, n_streams, per_stream, (uint32_t)prngd::kChunk, 32, 0);
 }
 
 // ----------------------------------------------------------------- fill dispatch

@@ -19,6 +19,7 @@ struct BatchShape {
   int warps_per_block;
   int blocks_per_sm;
   int items_per_ticket;
+  int outputs_per_chunk;  // outputs a lane makes between the warp's tensor stores (16 or 32)
 };
 }  // namespace prngd_host
 
@@ -73,6 +74,8 @@ cudaError_t launch_fill_map_fast(const prngd::FillParams& p, int form, int map, 
 int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
 bool device_mapped_host(const void* p, void** dev);
 bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream);
+bool encode_out_map_box(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream, uint32_t box_x,
+                        uint32_t box_y, uint64_t pitch);
 void release_aux(prng_ctx* h);
 void release_split(prng_ctx* h);
 int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64_t per_stream, int form,

@@ -6,7 +6,7 @@
 // combined as z = (x1 - x2) mod m1 in [1, m1] (0 reported as m1). The method reads z as the
 // draw u = z - 1 on a grid of M = m1 points with step k = 1/M, so Section 2 holds with 2^w
 // replaced by M: pairs with u1 in {0, M - 1} are rejected and z' = n / D with
-// n = u1 M + u2 - (M - 1), D = (M - 1)^2 < 2^64, converted by a series fast path (mrg_fast_I)
+// n = u1 M + u2 - (M - 1), D = (M - 1)^2 < 2^64, converted by a series fast path (mrg_fast_I_ab)
 // or exactly (Moller-Granlund division) for small values and margin cases.
 //
 // State: 32 bytes per stream in the handle's state array (two uint4: x1_{n-3}, x1_{n-2},
@@ -49,76 +49,143 @@ __global__ void mrg_seed_kernel(uint4* state, uint64_t n, uint64_t seed) {
   mrg_store(state, s, g);
 }
 
+#ifndef PRNGD_MRG_UNROLL
+#define PRNGD_MRG_UNROLL 4
+#endif
+// output pairs unrolled in a chunk's loop: measured (form B / balanced / C, Gsamples/s) 2: 283 /
+// 292 / 273, 4: 283 / 300 / 276, all 8: 279 / 302 / 276
+constexpr int kMrgUnroll = PRNGD_MRG_UNROLL;
+
+// The rare cases of an output, out of line so that the unrolled chunk stays within the
+// instruction cache (inline, the chunk stalled on instruction fetch: form B 260 -> 283
+// Gsamples/s out of line): a rejected pair (u1 in {0, M - 1}, probability 2/M) is followed by the
+// next pairs until one is accepted; small values and margin cases take the exact division.
+struct MrgRedraw {
+  Mrg32k3a g;
+  uint32_t rej, u1, u2;
+};
+__device__ __noinline__ MrgRedraw mrg_redraw(Mrg32k3a g, uint32_t rej) {
+  uint32_t u1, u2;
+  do {
+    ++rej;
+    u1 = mrg_next(g) - 1u;
+    u2 = mrg_next(g) - 1u;
+  } while (u1 - 1u >= kMrgM1 - 2u);
+  return MrgRedraw{g, rej, u1, u2};
+}
+__device__ __noinline__ uint64_t mrg_exact_bits(uint32_t u1, uint32_t u2, DivConst dc) {
+  return rn_bits_exact((uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u), dc);
+}
+
 // One output of the method over MRG32k3a draws (pair rule), 8 bytes of form FORM; MAP is 0 or
 // kMapCvt (PRNG_MODE_BALANCED, form B's rounding route).
 template <int FORM, int MAP = 0>
 __device__ __forceinline__ uint64_t mrg_next_output(Mrg32k3a& g, uint32_t& rej, const FillParams& p) {
   // the usual case, an accepted pair, is straight-line code (no loop around the state's
-  // rotation); a rejected pair (u1 in {0, M - 1}, probability 2/M) takes the next pair
+  // rotation)
   uint32_t u1 = mrg_next(g) - 1u;
   uint32_t u2 = mrg_next(g) - 1u;
   if (__builtin_expect(u1 - 1u >= kMrgM1 - 2u, 0)) {
-    do {
-      ++rej;
-      u1 = mrg_next(g) - 1u;
-      u2 = mrg_next(g) - 1u;
-    } while (u1 - 1u >= kMrgM1 - 2u);
+    const MrgRedraw r = mrg_redraw(g, rej);
+    g = r.g;
+    rej = r.rej;
+    u1 = r.u1;
+    u2 = r.u2;
   }
-  const uint64_t n = (uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u);
+  // n = u1 M + u2 - (M - 1), formed only where it is used
   // form A: the conversion instruction, then the scale (its definition's two FP64 steps)
-  if constexpr (FORM == kFormA) return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn(n), p.scale));
+  if constexpr (FORM == kFormA)
+    return (uint64_t)__double_as_longlong(__dmul_rn(__ull2double_rn((uint64_t)u1 * kMrgM1 + u2 - (kMrgM1 - 1u)), p.scale));
   uint64_t bits;
   uint32_t ok = 0;
   if (__builtin_expect(u1 > (1u << 22), 1)) {  // A >= 2^22: the series fast path
-    const uint64_t I = mrg_fast_I(n, ok);
+    const uint64_t I = mrg_fast_I_ab(u1 - 1u, u2 + 1u, ok);
     // the fills' rounding routes (cvt_group_mask): form C by the conversion instruction; form B
-    // by integer operations, or by the conversion under PRNG_MODE_BALANCED (measured 216 and
-    // 224 Gsamples/s)
+    // by integer operations, or by the conversion under PRNG_MODE_BALANCED (measured 283 and
+    // 300 Gsamples/s)
     bits = cvt_group_mask<FORM, 32, MAP>() ? bits_from_I_cvt(I, p.one) : bits_from_I_int(I, p.one);
   }
-  if (__builtin_expect(!ok, 0)) bits = rn_bits_exact(n, p.dc);  // small values, margin cases
+  if (__builtin_expect(!ok, 0)) {  // small values, margin cases
+    bits = mrg_exact_bits(u1, u2, p.dc);
+  }
   return FORM == kFormC ? f32pair_from_bits(bits) : bits;
 }
 
-// Tile-staged TMA path, as the xorshift fill kernel: warp g owns streams 32g .. 32g+31, 16
-// outputs per lane per chunk through a 128-byte-swizzled tile and one 2D tensor store.
-template <int FORM, int MAP = 0>
+// Tile-staged TMA path with SPT streams per thread and CH outputs per stream per chunk: warp g
+// owns the 32 SPT streams from 32 SPT g on, lane l runs streams 32 SPT g + 32 t + l (t < SPT),
+// and each chunk goes out as one 2D tensor store of a CH x 32 SPT box from the warp's tile.
+// Rows are CH * 8 bytes, swizzled in 128-byte (CH = 16: piece c of row r at
+// r 128 + (c ^ (r & 7)) 16) or 64-byte (CH = 8: r 64 + (c ^ ((r >> 1) & 3)) 16) mode, which
+// keeps the lanes' 16-byte stores free of bank conflicts.
+// Each step of x2's recurrence needs the previous value, so with one stream per thread the
+// issue slots idle while that chain's latency runs out; with two, the compiler interleaves
+// two independent chains. Outputs go to the tile two at a time as they are made, so no
+// register holds a whole chunk.
+template <int FORM, int MAP = 0, int SPT = 1, int CH = kChunk>
 __global__ void __launch_bounds__(256) fill_mrg_tma_kernel(const FillParams p, const __grid_constant__ CUtensorMap tmap) {
+  static_assert(CH == 16 || CH == 8, "rows of 128 or 64 bytes");
+  constexpr uint32_t kRowBytes = CH * 8;
+  constexpr uint32_t kWarpTile = 32u * SPT * kRowBytes;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t base = (smem_addr(smem_raw) + 1023u) & ~1023u;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   const uint64_t warp_global = (uint64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-  if (warp_global * 32 >= p.n_streams) return;
-  const uint64_t stream = warp_global * 32 + lane;
-  const bool active = stream < p.n_streams;
-  Mrg32k3a g = active ? mrg_load(p.state, stream) : Mrg32k3a{1u, 2u, 3u, 4u, 5u, 6u};
-  uint32_t rej = 0;
-  const uint32_t tile = base + (uint32_t)warp * kTileBytes;
-  const uint32_t row_off = (uint32_t)lane * 128u;
-  const uint32_t sw = (uint32_t)(lane & 7);
-  const int y0 = (int)(warp_global * 32);
-  for (uint64_t x0 = 0; x0 < p.per_stream; x0 += kChunk) {
-    uint64_t v[kChunk];
+  const uint64_t first = warp_global * 32 * SPT;
+  if (first >= p.n_streams) return;
+  Mrg32k3a g[SPT];
+  uint32_t rej[SPT];
+  uint32_t rowb[SPT];  // row address with the swizzle's xor pattern or-ed into bits 4..6
+  const uint32_t tile = base + (uint32_t)warp * kWarpTile;
+#pragma unroll
+  for (int t = 0; t < SPT; ++t) {
+    const uint64_t stream = first + 32 * t + lane;
+    g[t] = stream < p.n_streams ? mrg_load(p.state, stream) : Mrg32k3a{1u, 2u, 3u, 4u, 5u, 6u};
+    rej[t] = 0;
+    const uint32_t r = 32u * t + (uint32_t)lane;
+    rowb[t] = (tile + r * kRowBytes) | ((CH == 16 ? (r & 7u) : ((r >> 1) & 3u)) << 4);
+  }
+  for (uint64_t x0 = 0; x0 < p.per_stream; x0 += CH) {
     const uint64_t left = p.per_stream - x0;
-#pragma unroll
-    for (int j = 0; j < kChunk; ++j) v[j] = ((uint64_t)j < left) ? mrg_next_output<FORM, MAP>(g, rej, p) : 0ull;
-    if (lane == 0) bulk_wait_read<0>();
+    if (lane == 0) bulk_wait_read<0>();  // the previous chunk's store has read the tile
     __syncwarp();
+    if (left >= (uint64_t)CH) {
+#pragma unroll kMrgUnroll
+      for (int c = 0; c < CH / 2; ++c) {
+        uint64_t v0[SPT], v1[SPT];
 #pragma unroll
-    for (int c = 0; c < kChunk / 2; ++c)
-      st_shared_v2(((tile + row_off) | (sw << 4)) ^ ((uint32_t)c << 4), v[2 * c], v[2 * c + 1]);  // as the fill
+        for (int t = 0; t < SPT; ++t) v0[t] = mrg_next_output<FORM, MAP>(g[t], rej[t], p);
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) v1[t] = mrg_next_output<FORM, MAP>(g[t], rej[t], p);
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) st_shared_v2(rowb[t] ^ ((uint32_t)c << 4), v0[t], v1[t]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < CH / 2; ++c) {
+#pragma unroll
+        for (int t = 0; t < SPT; ++t) {
+          const uint64_t a = ((uint64_t)(2 * c) < left) ? mrg_next_output<FORM, MAP>(g[t], rej[t], p) : 0ull;
+          const uint64_t b = ((uint64_t)(2 * c + 1) < left) ? mrg_next_output<FORM, MAP>(g[t], rej[t], p) : 0ull;
+          st_shared_v2(rowb[t] ^ ((uint32_t)c << 4), a, b);
+        }
+      }
+    }
     fence_async_shared();
     __syncwarp();
-    if (lane == 0) {
-      tma_store_2d(&tmap, tile, (int)x0, y0);
+    if (lane == 0) {  // rows past the last stream and columns past per_stream are clipped
+      tma_store_2d(&tmap, tile, (int)x0, (int)first);
       bulk_commit();
     }
   }
   if (lane == 0) bulk_wait_all();
-  if (active) {
-    mrg_store(p.state, stream, g);
-    if (p.rejects) p.rejects[stream] = rej;
+#pragma unroll
+  for (int t = 0; t < SPT; ++t) {
+    const uint64_t stream = first + 32 * t + lane;
+    if (stream < p.n_streams) {
+      mrg_store(p.state, stream, g[t]);
+      if (p.rejects) p.rejects[stream] = rej[t];
+    }
   }
 }
 
@@ -153,19 +220,28 @@ static prngd::DivConst mrg_divconst() {
 
 namespace {
 constexpr int kWarpsPerBlock = 8;
-constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * prngd::kTileBytes + 1024;
+#ifndef PRNGD_MRG_SPT
+#define PRNGD_MRG_SPT 1
+#endif
+#ifndef PRNGD_MRG_CHUNK
+#define PRNGD_MRG_CHUNK 16
+#endif
+constexpr int kSpt = PRNGD_MRG_SPT;    // streams per thread of the TMA path
+constexpr int kCh = PRNGD_MRG_CHUNK;   // outputs per stream per staged chunk
+constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * 32 * kSpt * kCh * 8 + 1024;
 
 template <int FORM, int MAP = 0>
 cudaError_t launch_mrg_form(const prngd::FillParams& p, const CUtensorMap* map, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((p.n_streams + 255) / 256);
   if (map) {
-    auto k = prngd::fill_mrg_tma_kernel<FORM, MAP>;
+    const uint64_t per_block = (uint64_t)kWarpsPerBlock * 32 * kSpt;
+    const unsigned blocks = (unsigned)((p.n_streams + per_block - 1) / per_block);
+    auto k = prngd::fill_mrg_tma_kernel<FORM, MAP, kSpt, kCh>;
     static std::atomic<uint64_t> attr{0};
     const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
     if (e != cudaSuccess) return e;
     k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
   } else {
-    prngd::fill_mrg_plain_kernel<FORM, MAP><<<blocks, 256, 0, s>>>(p);
+    prngd::fill_mrg_plain_kernel<FORM, MAP><<<(unsigned)((p.n_streams + 255) / 256), 256, 0, s>>>(p);
   }
   return cudaGetLastError();
 }
@@ -192,7 +268,8 @@ int launch_fill_mrg(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, ui
   p.w = 32;
   p.one = 1;
   CUtensorMap map;
-  const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
+  const CUtensorMap* mp =
+      (allow_tma && encode_out_map_box(&map, out, n_streams, per_stream, (uint32_t)kCh, 32u * kSpt, 0)) ? &map : nullptr;
   cudaError_t e;
   switch (form) {
     case PRNG_FORM_A_FP64: e = launch_mrg_form<prngd::kFormA>(p, mp, s); break;

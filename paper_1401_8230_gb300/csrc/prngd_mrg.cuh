@@ -15,6 +15,12 @@ struct Mrg32k3a {
   uint32_t b0, b1, b2;  // x2_{n-3}, x2_{n-2}, x2_{n-1}
 };
 
+// The canonical residue of r < 2^32 modulo m = 2^32 - d (d < m): r - m wraps to r + d, which is
+// larger than r exactly when r < m, so the smaller of the two is r mod m.
+PRNGD_HD uint32_t canon(uint32_t r, uint32_t d) {
+  const uint32_t s = r + d;
+  return s < r ? s : r;
+}
 // v mod m1 for v < 2^54, folding 2^32 = 209 (mod m1) in 32-bit arithmetic: the high word times
 // 209 is below 2^30, and a carry out of adding it to the low word (the sum then < 2^30) folds
 // once more as + 209.
@@ -22,7 +28,7 @@ PRNGD_HD uint32_t mod_m1(uint64_t v) {
   const uint32_t t = (uint32_t)(v >> 32) * 209u;
   uint32_t r = (uint32_t)v + t;
   if (r < t) r += 209u;
-  return r >= kMrgM1 ? r - kMrgM1 : r;
+  return canon(r, 209u);
 }
 // v mod m2 for v < 2^54, folding 2^32 = 22853 (mod m2): after one wide fold w < 2^37, whose
 // high word (< 32) folds with a 32-bit multiply; a carry out of that add (the sum then < 2^20)
@@ -32,7 +38,7 @@ PRNGD_HD uint32_t mod_m2(uint64_t v) {
   const uint32_t t = (uint32_t)(w >> 32) * 22853u;  // < 2^20
   uint32_t r = (uint32_t)w + t;
   if (r < t) r += 22853u;
-  return r >= kMrgM2 ? r - kMrgM2 : r;
+  return canon(r, 22853u);
 }
 
 // One step; returns z in [1, m1]. The negative terms are made positive by adding a multiple of
@@ -49,23 +55,20 @@ PRNGD_HD uint32_t mrg_next(Mrg32k3a& g) {
   return p1 > p2 ? p1 - p2 : p1 - p2 + kMrgM1;
 }
 
-// Fast path of floor(V 2^64), V = n / D, D = (m1 - 1)^2 = (2^32 - 210)^2, n = A m1 + B < 2^64.
-// With c = 210 2^-32, 2^64 / D = sum (i + 1) c^i, so with n = nh 2^32 + nl
-//   V 2^64 = n + E0 + E1 2^-32 + E2 2^-64 + eps,
-//   E0 = 420 nh, E1 = 420 nl + 132300 nh, E2 = 132300 nl + 37044000 nh,
-// 0 <= eps < 5.4e-10 (37044000 nl 2^-96 and the terms from 5 c^4 n on). With S = E1 + (E2 >> 32)
-// the exact value is n + E0 + (S + r) 2^-32 with 0 <= r < 3.3, so the integer part is
-// n + E0 + (S >> 32) unless the low word of S lies within 16 of 2^32 (`ok` = 0). For A >= 2^22
-// it is at least 2^54, and it rounds like the xorshift fast path's I.
-PRNGD_HD uint64_t mrg_fast_I(uint64_t n, uint32_t& ok) {
-  // the halves as 32-bit values, so that every product is one 32 x 32 -> 64 multiply(-add)
-  const uint32_t nh = (uint32_t)(n >> 32), nl = (uint32_t)n;
-  const uint64_t E0 = (uint64_t)nh * 420u;
-  const uint64_t E1 = (uint64_t)nl * 420u + (uint64_t)nh * 132300u;
-  const uint64_t E2 = (uint64_t)nl * 132300u + (uint64_t)nh * 37044000u;
-  const uint64_t S = E1 + (E2 >> 32);
+// Fast path of floor(V 2^64), V = n / D, D = (M - 1)^2, from A = u1 - 1 and B = u2 + 1
+// (n = A M + B, M = m1) without forming n. With M - 1 = 2^32 (1 - c), c = 210 2^-32, V = A / (M - 1) + (A + B) / (M - 1)^2 expands as
+//   V 2^64 = A 2^32 + (211 A + B) + (44520 A + 420 B) 2^-32 + (9393300 A + 132300 B) 2^-64 + R,
+// every term of R positive and R 2^32 < 0.47 (largest at A = M - 3, B = M). With
+// S = 44520 A + 420 B + ((9393300 A + 132300 B) >> 32) the part below 2^-32 adds less than 1.47
+// to S, so floor(V 2^64) = A 2^32 + 211 A + B + (S >> 32) unless S's low word is within 16 of
+// 2^32 (`ok` = 0). Every product is one 32 x 32 -> 64 multiply(-add). For A >= 2^22 the result
+// is at least 2^54, and it rounds like the xorshift fast path's I.
+PRNGD_HD uint64_t mrg_fast_I_ab(uint32_t A, uint32_t B, uint32_t& ok) {
+  const uint64_t W = (uint64_t)A * 9393300u + (uint64_t)B * 132300u;
+  const uint64_t S = (uint64_t)A * 44520u + (uint64_t)B * 420u + (uint32_t)(W >> 32);
   ok = ((uint32_t)S < 0xFFFFFFF0u) ? 1u : 0u;
-  return n + E0 + (S >> 32);
+  const uint64_t Y = (uint64_t)A * 211u + B + (uint32_t)(S >> 32);
+  return ((uint64_t)A << 32) + Y;
 }
 
 }  // namespace prngd

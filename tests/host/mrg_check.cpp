@@ -63,41 +63,46 @@ int main() {
       check_mod(k * m2 + (uint64_t)(int64_t)d);
     }
   check_mod((1ull << 54) - 1);
-  // the conversion's fast path: floor(n 2^64 / D) exactly wherever it reports ok, on random n,
-  // on n of each binade's ends, and on n placing the low word of S next to 2^32
   const unsigned __int128 D = (unsigned __int128)(m1 - 1u) * (m1 - 1u);
-  auto check_fast = [&](uint64_t n) {
-    if (n == 0 || (unsigned __int128)n >= D) return;
+  // the conversion's fast path from A = u1 - 1 and B = u2 + 1: floor(n 2^64 / D) exactly wherever
+  // it reports ok, on random pairs, at the ends of both ranges, and on B placing the low word of
+  // S next to 2^32
+  const uint64_t M = m1;
+  long near_ab = 0, refused_ab = 0;
+  auto check_ab = [&](uint64_t A, uint64_t B) {
+    if (A < (1u << 22) || A > M - 3 || B < 1 || B > M) return;
     uint32_t ok;
-    const uint64_t I = mrg_fast_I(n, ok);
-    if (!ok) return;
+    const uint64_t I = mrg_fast_I_ab((uint32_t)A, (uint32_t)B, ok);
+    if (!ok) {
+      ++refused_ab;
+      return;
+    }
     ++checked;
-    const uint64_t want = (uint64_t)(((unsigned __int128)n << 64) / D);
+    const uint64_t want = (uint64_t)(((unsigned __int128)(A * M + B) << 64) / D);
     if (I != want) {
-      if (bad < 10) printf("mrg_fast_I mismatch n=%llu\n", (unsigned long long)n);
+      if (bad < 10) printf("mrg_fast_I_ab mismatch A=%llu B=%llu\n", (unsigned long long)A, (unsigned long long)B);
       ++bad;
     }
   };
-  for (int i = 0; i < 4000000; ++i) check_fast(rng() % (uint64_t)((m1 - 1ull) * (m1 - 1ull)));
-  for (int p = 54; p < 64; ++p)
-    for (int d = -64; d < 64; ++d) check_fast((1ull << p) + (uint64_t)(int64_t)d);
-  long near = 0;
-  for (int i = 0; i < 400000; ++i) {  // nl solving 420 nl = k 2^32 - (132300 nh mod 2^32) - d: S's low
-    const uint64_t nh = rng() % (m1 - 2u);       // word lands within a few hundred of 2^32
-    const uint64_t k = 1 + rng() % 419, d = rng() % 600;
-    uint64_t nl = 0;
-    for (int it = 0; it < 2; ++it) {  // the carry term (E2 >> 32) depends on nl: refine once
-      const uint64_t e = (132300u * nl + 37044000u * nh) >> 32;
-      const int64_t num = (int64_t)((k << 32) - ((132300u * nh + e) & 0xFFFFFFFFull)) - (int64_t)d;
-      nl = num < 0 ? (1ull << 40) : (uint64_t)num / 420u;
+  for (int i = 0; i < 4000000; ++i) check_ab((1u << 22) + rng() % (M - 2 - (1u << 22)), 1 + rng() % M);
+  for (uint64_t A : {(uint64_t)1 << 22, ((uint64_t)1 << 22) + 1, M / 2, M - 4, M - 3})
+    for (uint64_t B : {(uint64_t)1, (uint64_t)2, M / 2, M - 1, M}) check_ab(A, B);
+  for (int i = 0; i < 400000; ++i) {  // B solving 44520 A + 420 B + (W >> 32) = k 2^32 - d
+    const uint64_t A = (1u << 22) + rng() % (M - 2 - (1u << 22));
+    const uint64_t d = rng() % 600;
+    uint64_t B = 1 + rng() % M;
+    for (int it = 0; it < 2; ++it) {  // (W >> 32) depends on B: refine once
+      const uint64_t wh = (9393300u * A + 132300u * B) >> 32;
+      const uint64_t base = 44520u * A + wh;
+      const uint64_t T = ((base + 420u * B) >> 32 << 32) + (1ull << 32) - d;  // the next boundary, minus d
+      B = (T - base) / 420u;
     }
-    if (nl > 0xFFFFFFFFull) continue;
-    const uint64_t n = (nh << 32) | nl;
-    const uint64_t S = 420u * nl + 132300u * nh + ((132300u * nl + 37044000u * nh) >> 32);
-    if ((uint32_t)S >= 0xFFFFF000u) ++near;
-    check_fast(n);
+    const uint64_t wh = (9393300u * A + 132300u * B) >> 32;
+    const uint64_t S = 44520u * A + 420u * B + wh;
+    if ((uint32_t)S >= 0xFFFFF000u) ++near_ab;
+    check_ab(A, B);
   }
-  printf("near-margin samples %ld\n", near);
+  printf("near-margin samples (A, B) %ld refused %ld\n", near_ab, refused_ab);
   printf("checked %ld bad %ld\n", checked, bad);
   return bad != 0;
 }

@@ -23,5 +23,6 @@ def test_mrg_step_matches_oracle(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout[-2000:]
     assert "bad 0" in out.stdout
-    near = int(out.stdout.split("near-margin samples")[1].split()[0])
-    assert near > 10000, near  # the fast path's margin was reached
+    near_ab = int(out.stdout.split("near-margin samples (A, B) ")[1].split()[0])
+    refused_ab = int(out.stdout.split("refused ")[1].split()[0])
+    assert near_ab > 10000 and refused_ab > 100, (near_ab, refused_ab)  # the fast path's margin was reached
