@@ -551,6 +551,14 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates
     torch.cuda.empty_cache()
     pool, reqs, arr = place(32, F)  # 256-byte aligned, the bench step's route
     ms = batch_ms(arr)
+    default_shape = P.prng_batch_get_shape(g.h)
+    default_ms = None
+    if tuned:  # the same batch with the untuned shape
+        P.prng_batch_set_shape(g.h, 8, 3, 4, 16)
+        default_shape = P.prng_batch_get_shape(g.h)
+        default_ms = batch_ms(arr)
+        P.prng_batch_set_shape(g.h, tuned["warps_per_block"], tuned["blocks_per_sm"], tuned["items_per_ticket"],
+                               tuned["outputs_per_chunk"])
     # plain: one launch per request on the same stream
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
@@ -584,7 +592,11 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates
             "eq5_map": {"gsamples_s": eq5, "ms": eq5_ms, "kernel": "any-mode",
                         "vs_plain_eq5_fill": (eq5 / eq5_plain) if eq5_plain else None},
             "per_request_launches_gsamples_s": total / (plain_ms * 1e-3) / 1e9,
-            "per_request_launches_ms": plain_ms, "shape": tuned, "graph": True}
+            "per_request_launches_ms": plain_ms, "shape": tuned, "graph": True,
+            "default_shape": {"warps_per_block": default_shape[0], "blocks_per_sm": default_shape[1],
+                              "items_per_ticket": default_shape[2], "outputs_per_chunk": default_shape[3],
+                              "ms": default_ms,
+                              "gsamples_s": (total / (default_ms * 1e-3) / 1e9) if default_ms else None}}
 
 
 def served(torch, P, plain_rate, seconds, mix_rate=None):

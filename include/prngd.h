@@ -349,27 +349,34 @@ int prng_poll(prng_t h, uint64_t ticket, int* done);
  * seconds. Errors: PRNG_ETIMEOUT, PRNG_ENOTFOUND, PRNG_ECUDA. */
 int prng_wait(prng_t h, uint64_t ticket, double timeout_s);
 
-/* Launch shape of the batch kernel: warps per block (1..8), blocks per SM (1..16) and items
- * taken per counter increment (1..64). Changing it never changes outputs; set_shape waits
- * for in-flight batches and re-captures the graphs on next use. */
-int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket);
-int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket);
+/* Launch shape of the batch kernel: warps per block (1..8), blocks per SM (1..16), items
+ * (32 rows of one request) taken per counter increment (1..64), and outputs per chunk (16 or
+ * 32): how many outputs each thread makes for its row before the warp writes them with
+ * tensor stores (32: two stores of 32 x 16 boxes; it applies to batches whose requests all use
+ * mode 0 or all form B with exactly PRNG_MODE_BALANCED, the others use 16). Changing the shape
+ * never changes outputs; set_shape waits for in-flight batches and re-captures the graphs on
+ * next use. Errors: PRNG_EINVAL (a value out of range), PRNG_ENOMEM, PRNG_ECUDA. */
+int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket,
+                         int* outputs_per_chunk);
+int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket,
+                         int outputs_per_chunk);
 
 /*
  * prng_batch_autotune -- pick the batch launch shape for requests of `form` with lengths in
  * [length_lo, length_hi]. If table_path names a table with a line for this (GPU name, w,
  * form, length range) and force == 0, that shape is applied without measuring. Otherwise
- * every candidate (4 or 8 warps per block x 2..8 blocks per SM x 1, 2 or 8 items per ticket)
- * is timed on a synthetic batch of 256 fresh requests with log-uniform lengths in the range
- * (at most 2^30 outputs, in an 8 GiB scratch buffer the call allocates and frees), the fastest is
- * applied and, if table_path is not NULL, appended to the table as
- * "<key> <warps> <blocks> <items> <ms>". Outputs never depend on the shape.
+ * every candidate (4 or 8 warps per block x 2, 3, 4, 6 or 8 blocks per SM x 1, 4 or 8 items
+ * per ticket x 16 or 32 outputs per chunk) is timed on a synthetic batch of 256 fresh requests
+ * with log-uniform lengths in the range (at most 2^30 outputs, in an 8 GiB scratch buffer the
+ * call allocates and frees), the fastest is applied and, if table_path is not NULL, appended to
+ * the table as "<key> <warps> <blocks> <items> <outputs per chunk> <ms>". Outputs never depend
+ * on the shape.
  * The chosen shape and its time (ms; -1 when read from the table) are returned through the
  * nullable pointers. Errors: PRNG_EINVAL, PRNG_ENOMEM, PRNG_ECUDA.
  */
 int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_hi, const char* table_path,
                         int force, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket,
-                        double* best_ms);
+                        int* outputs_per_chunk, double* best_ms);
 
 /*
  * Serving loop. A server keeps per-client generator state resident on the device and runs

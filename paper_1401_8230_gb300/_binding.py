@@ -68,10 +68,12 @@ _SIGNATURES = {
     "prng_submit": (_i32, [_P, ctypes.c_void_p, _i32, ctypes.POINTER(_u64), _vp]),
     "prng_poll": (_i32, [_P, _u64, ctypes.POINTER(_i32)]),
     "prng_wait": (_i32, [_P, _u64, _dbl]),
-    "prng_batch_get_shape": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
-    "prng_batch_set_shape": (_i32, [_P, _i32, _i32, _i32]),
+    "prng_batch_get_shape": (_i32, [_P, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                    ctypes.POINTER(_i32)]),
+    "prng_batch_set_shape": (_i32, [_P, _i32, _i32, _i32, _i32]),
     "prng_batch_autotune": (_i32, [_P, _i32, _u64, _u64, ctypes.c_char_p, _i32, ctypes.POINTER(_i32),
-                                   ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_dbl)]),
+                                   ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                   ctypes.POINTER(_dbl)]),
     "prng_server_create": (_i32, [ctypes.POINTER(_P), _P, _u64, _u64, _sz]),
     "prng_server_destroy": (_i32, [_P]),
     "prng_server_submit": (_i32, [_P, _u64, _u64, _i32, ctypes.POINTER(_u64)]),
@@ -246,23 +248,25 @@ def prng_wait(h: int, ticket: int, timeout_s: float = 60.0) -> None:
     _check(lib().prng_wait(h, ticket, timeout_s))
 
 
-def prng_batch_get_shape(h: int) -> tuple[int, int, int]:
-    a, b, c = _i32(), _i32(), _i32()
-    _check(lib().prng_batch_get_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-    return a.value, b.value, c.value
+def prng_batch_get_shape(h: int) -> tuple[int, int, int, int]:
+    a, b, c, d = _i32(), _i32(), _i32(), _i32()
+    _check(lib().prng_batch_get_shape(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
 
 
-def prng_batch_set_shape(h: int, warps_per_block: int, blocks_per_sm: int, items_per_ticket: int) -> None:
-    _check(lib().prng_batch_set_shape(h, warps_per_block, blocks_per_sm, items_per_ticket))
+def prng_batch_set_shape(h: int, warps_per_block: int, blocks_per_sm: int, items_per_ticket: int,
+                         outputs_per_chunk: int = 16) -> None:
+    _check(lib().prng_batch_set_shape(h, warps_per_block, blocks_per_sm, items_per_ticket, outputs_per_chunk))
 
 
 def prng_batch_autotune(h: int, form: int, length_lo: int, length_hi: int, table_path: str | None = None,
                         force: bool = False) -> dict:
-    a, b, c, ms = _i32(), _i32(), _i32(), _dbl()
+    a, b, c, d, ms = _i32(), _i32(), _i32(), _i32(), _dbl()
     path = table_path.encode() if table_path else None
     _check(lib().prng_batch_autotune(h, form, length_lo, length_hi, path, int(force), ctypes.byref(a), ctypes.byref(b),
-                                     ctypes.byref(c), ctypes.byref(ms)))
-    return {"warps_per_block": a.value, "blocks_per_sm": b.value, "items_per_ticket": c.value, "ms": ms.value}
+                                     ctypes.byref(c), ctypes.byref(d), ctypes.byref(ms)))
+    return {"warps_per_block": a.value, "blocks_per_sm": b.value, "items_per_ticket": c.value,
+            "outputs_per_chunk": d.value, "ms": ms.value}
 
 
 def prng_server_create(h: int, streams_per_client: int, min_per_stream: int = 256, pool_bytes: int = 32 << 30) -> int:

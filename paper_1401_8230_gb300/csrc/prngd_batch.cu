@@ -90,21 +90,25 @@ static int ensure_engine(prng_ctx* h) {
   return PRNG_OK;
 }
 
-// 8 warps x 3 blocks (all resident at the kernel's register count) taking 4 items per ticket:
-// the fastest untuned shape on the batched workload with aligned outputs.
+// 8 warps x 3 blocks (all resident at the kernel's register count) taking 4 items per ticket,
+// 16 outputs per chunk: the fastest untuned shape on the batched workload with aligned outputs.
 BatchShape default_batch_shape(int num_sms) {
   BatchShape s;
   s.warps_per_block = 8;
   s.blocks_per_sm = 3;
   s.items_per_ticket = 4;
+  s.outputs_per_chunk = prngd::kChunk;
   (void)num_sms;
   return s;
 }
 
 template <int W, int FORM_ALL>
 static cudaError_t launch_batch_wf(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
-  return prngd::launch_batch_kernel<W, FORM_ALL>(p, sh.warps_per_block, (unsigned)(num_sms * sh.blocks_per_sm),
-                                                 PRNG_MAX_BATCH_REQUESTS, s);
+  const unsigned blocks = (unsigned)(num_sms * sh.blocks_per_sm);
+  if (sh.outputs_per_chunk == 2 * prngd::kChunk)
+    return prngd::launch_batch_kernel<W, FORM_ALL, 2 * prngd::kChunk>(p, sh.warps_per_block, blocks,
+                                                                      PRNG_MAX_BATCH_REQUESTS, s);
+  return prngd::launch_batch_kernel<W, FORM_ALL>(p, sh.warps_per_block, blocks, PRNG_MAX_BATCH_REQUESTS, s);
 }
 
 template <int W>
@@ -268,7 +272,14 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
   sl->h_meta[1 + n] = (uint32_t)acc;
   for (int i = 0; i < n; ++i) {  // 2D maps of the full rows; a request without one uses plain stores
     prngd::BatchDesc& q = sl->h_desc[i];
-    if (q.full_rows < 32 || !encode_out_map(&sl->h_maps[i], q.out, q.full_rows, q.per_stream)) q.full_rows = 0;
+    // rows that all start 16 bytes into a 32-byte sector: the map covers outputs 2 .. per_stream - 1
+    // of each row, so that every tensor store writes whole sectors (batch_item_full)
+    q.shift = (((uintptr_t)q.out & 31) == 16 && (q.per_stream & 3) == 0 && q.per_stream > 2) ? 1 : 0;
+    const bool mapped =
+        q.shift ? encode_out_map_box(&sl->h_maps[i], q.out + 2, q.full_rows, q.per_stream - 2,
+                                     (uint32_t)prngd::kChunk, 32, q.per_stream * 8)
+                : encode_out_map(&sl->h_maps[i], q.out, q.full_rows, q.per_stream);
+    if (q.full_rows < 32 || !mapped) q.full_rows = 0;
   }
   // kernel: one form, mode 0 -> a single-form kernel; form B with exactly PRNG_MODE_BALANCED
   // -> its single-form kernel; forms A, B, C, mode 0 -> the mixed-form kernel; otherwise the
@@ -322,7 +333,8 @@ int set_batch_shape(prng_ctx* h, const BatchShape& sh) {
   int rc = ensure_engine(h);
   if (rc) return rc;
   if (sh.warps_per_block < 1 || sh.warps_per_block > 8 || sh.blocks_per_sm < 1 || sh.blocks_per_sm > 16 ||
-      sh.items_per_ticket < 1 || sh.items_per_ticket > 64)
+      sh.items_per_ticket < 1 || sh.items_per_ticket > 64 ||
+      (sh.outputs_per_chunk != prngd::kChunk && sh.outputs_per_chunk != 2 * prngd::kChunk))
     return fail(PRNG_EINVAL, "batch shape out of range");
   for (auto& s : h->batch->slot)
     if (s.ticket && cudaEventSynchronize(s.done) != cudaSuccess) return fail(PRNG_ECUDA, "sync before reshape");
@@ -342,7 +354,8 @@ int get_batch_shape(prng_ctx* h, BatchShape* sh) {
 // Times each candidate launch shape on a synthetic batch of fresh requests whose lengths are
 // log-uniform in [lo, hi] (deterministic, at most 2^30 outputs in total, 256-byte aligned
 // outputs) and keeps the fastest.
-// Results are cached in a text table, one line per key: "<key> <warps> <blocks> <items> <ms>".
+// Results are cached in a text table, one line per key:
+// "<key> <warps> <blocks> <items> <outputs per chunk> <ms>".
 static std::string tune_key(prng_ctx* h, int form, uint64_t lo, uint64_t hi) {
   cudaDeviceProp pr;
   std::string name = "gpu";
@@ -360,12 +373,12 @@ static bool table_lookup(const char* path, const std::string& key, BatchShape* s
   FILE* f = fopen(path, "r");
   if (!f) return false;
   char k[256];
-  int a, b, c;
+  int a, b, c, d;
   double ms;
   bool found = false;
-  while (fscanf(f, "%255s %d %d %d %lf", k, &a, &b, &c, &ms) == 5)
+  while (fscanf(f, "%255s %d %d %d %d %lf", k, &a, &b, &c, &d, &ms) == 6)
     if (key == k) {
-      *sh = BatchShape{a, b, c};
+      *sh = BatchShape{a, b, c, d};
       found = true;
     }
   fclose(f);
@@ -433,15 +446,16 @@ int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, 
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   cudaEventCreate(&a);
   cudaEventCreate(&b);
-  const int W[] = {4, 8}, B[] = {2, 3, 4, 6, 8}, I[] = {1, 4, 8};
+  const int W[] = {4, 8}, B[] = {2, 3, 4, 6, 8}, I[] = {1, 4, 8}, C[] = {prngd::kChunk, 2 * prngd::kChunk};
   BatchShape best = default_batch_shape(h->num_sms);
   double best_t = 1e30;
   int rc = PRNG_OK;
+  for (int cv : C)
   for (int wv : W)
     for (int bv : B)
       for (int iv : I) {
         if (rc) break;
-        rc = set_batch_shape(h, BatchShape{wv, bv, iv});
+        rc = set_batch_shape(h, BatchShape{wv, bv, iv, cv});
         uint64_t t = 0;
         if (!rc) rc = submit(h, reqs.data(), n, &t, st);  // warm-up (captures the graph)
         if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = fail(PRNG_ECUDA, "autotune sync");
@@ -457,7 +471,7 @@ int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, 
         std::sort(times, times + 3);
         if (times[1] < best_t) {
           best_t = times[1];
-          best = BatchShape{wv, bv, iv};
+          best = BatchShape{wv, bv, iv, cv};
         }
       }
   cudaStreamSynchronize(st);
@@ -471,8 +485,8 @@ int autotune(prng_ctx* h, int form, uint64_t lo, uint64_t hi, const char* path, 
   if (path) {
     FILE* f = fopen(path, "a");
     if (f) {
-      fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), best.warps_per_block, best.blocks_per_sm, best.items_per_ticket,
-              best_t);
+      fprintf(f, "%s %d %d %d %d %.6f\n", key.c_str(), best.warps_per_block, best.blocks_per_sm, best.items_per_ticket,
+              best.outputs_per_chunk, best_t);
       fclose(f);
     }
   }
@@ -513,7 +527,8 @@ int prng_wait(prng_t h, uint64_t ticket, double timeout_s) {
   }
 }
 
-int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket) {
+int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket,
+                         int* outputs_per_chunk) {
   if (!h) return fail(PRNG_EINVAL, "null handle");
   BatchShape sh;
   int rc = get_batch_shape(h, &sh);
@@ -521,11 +536,13 @@ int prng_batch_get_shape(prng_t h, int* warps_per_block, int* blocks_per_sm, int
   if (warps_per_block) *warps_per_block = sh.warps_per_block;
   if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
   if (items_per_ticket) *items_per_ticket = sh.items_per_ticket;
+  if (outputs_per_chunk) *outputs_per_chunk = sh.outputs_per_chunk;
   return PRNG_OK;
 }
 
 int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_hi, const char* table_path,
-                        int force, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket, double* best_ms) {
+                        int force, int* warps_per_block, int* blocks_per_sm, int* items_per_ticket,
+                        int* outputs_per_chunk, double* best_ms) {
   if (!h) return fail(PRNG_EINVAL, "null handle");
   if (form != PRNG_FORM_A_FP64 && form != PRNG_FORM_B_INTBITS && form != PRNG_FORM_C_F32PAIR)
     return fail(PRNG_EINVAL, "form %d", form);
@@ -537,12 +554,14 @@ int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_
   if (warps_per_block) *warps_per_block = sh.warps_per_block;
   if (blocks_per_sm) *blocks_per_sm = sh.blocks_per_sm;
   if (items_per_ticket) *items_per_ticket = sh.items_per_ticket;
+  if (outputs_per_chunk) *outputs_per_chunk = sh.outputs_per_chunk;
   return PRNG_OK;
 }
 
-int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket) {
+int prng_batch_set_shape(prng_t h, int warps_per_block, int blocks_per_sm, int items_per_ticket,
+                         int outputs_per_chunk) {
   if (!h) return fail(PRNG_EINVAL, "null handle");
-  BatchShape sh{warps_per_block, blocks_per_sm, items_per_ticket};
+  BatchShape sh{warps_per_block, blocks_per_sm, items_per_ticket, outputs_per_chunk};
   return set_batch_shape(h, sh);
 }
 

@@ -27,7 +27,9 @@ struct BatchDesc {       // 64 bytes, built on the host
   uint64_t* rejects;     // nullable, one count per row
   uint32_t n_rows;       // streams used
   int32_t form;          // kFormA / kFormB / kFormC / kFormL
-  uint16_t resident;     // 1: rows continue handle streams
+  uint8_t resident;      // 1: rows continue handle streams
+  uint8_t shift;         // 1: rows start 16 bytes into a 32-byte sector; the request's map then
+                         // starts 2 outputs into each row (see batch_item_full)
   uint16_t mode;         // PRNG_MODE_* bits: Eq. 5 map, 1 - z, Algorithm 1's single redraw
   uint32_t full_rows;    // rows 0 .. full_rows-1 hold per_stream outputs and are covered by the
                          // request's tensor map (0: no map, plain stores only)
@@ -75,14 +77,17 @@ __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
 // no longer fits the instruction cache. Lane 0 waits for the warp's previous tensor store to
 // have read the tile before the first piece is written.
 // CVT: the outputs of each 4-output step rounded by the conversion instruction (cvt_group_mask).
-template <int W, int FORM, int MAP, uint32_t CVT>
+// CH = 32: 32 outputs as two 32 x 16 sub-tiles 4 KiB apart (pieces 8..15 of the row in the
+// second), each with the same swizzle.
+template <int W, int FORM, int MAP, uint32_t CVT, int CH = kChunk>
 __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej, const FillParams& fp,
                                                  uint32_t my_row, uint32_t sw, int lane) {
+  static_assert(CH == kChunk || CH == 2 * kChunk, "one or two sub-tiles");
   // my_row has zero bits 4..6 (1024-byte aligned tile, 128-byte rows): piece c lies at
   // (my_row | (sw << 4)) ^ 16c, and the loop counts c4 = 16c
   const uint32_t rowb = my_row | (sw << 4);
 #pragma unroll 1
-  for (uint32_t c4 = 0; c4 < (uint32_t)kChunk * 8u; c4 += 32u) {
+  for (uint32_t c4 = 0; c4 < (uint32_t)CH * 8u; c4 += 32u) {
     uint64_t a0, a1, b0, b1;
     if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
       next_pair<W, FORM, MAP>(st, rej, fp, a0, a1, CVT & 1u, (CVT >> 1) & 1u);
@@ -97,8 +102,10 @@ __device__ __forceinline__ void stage_full_chunk(XorShift128& st, uint32_t& rej,
       if (lane == 0) bulk_wait_read<0>();
       __syncwarp();
     }
-    st_shared_v2(rowb ^ c4, a0, a1);
-    st_shared_v2(rowb ^ c4 ^ 16u, b0, b1);
+    uint32_t a = rowb ^ c4;
+    if constexpr (CH == 2 * kChunk) a = (rowb + ((c4 >> 7) << 12)) ^ (c4 & 0x70u);  // sub-tile c / 8
+    st_shared_v2(a, a0, a1);
+    st_shared_v2(a ^ 16u, b0, b1);
   }
 }
 
@@ -143,6 +150,20 @@ __device__ __noinline__ RowState stage_partial_chunk(RowState rs, const BatchPar
   return RowState{st, rej};
 }
 
+// The first two outputs of a row whose request is shifted (BatchDesc::shift). Out of line: once
+// per row.
+struct RowHead {
+  RowState rs;
+  uint64_t v0, v1;
+};
+template <int W, int FORM, int MAP>
+__device__ __noinline__ RowHead row_head(RowState rs, const BatchParams& bp, uint32_t single) {
+  const FillParams fp = fill_params_of<MAP>(bp, single);
+  const uint64_t v0 = next_output<W, FORM, MAP>(rs.st, rs.rej, fp);
+  const uint64_t v1 = next_output<W, FORM, MAP>(rs.st, rs.rej, fp);
+  return RowHead{rs, v0, v1};
+}
+
 // Stream state of row `row` of a request at its first output.
 __device__ __forceinline__ XorShift128 item_row_state(const BatchDesc* __restrict__ dp, const BatchParams& bp,
                                                       uint64_t row) {
@@ -156,8 +177,16 @@ __device__ __forceinline__ XorShift128 item_row_state(const BatchDesc* __restric
 // An item of 32 full rows (every row holds per_stream outputs): rows row0 .. row0 + 31 of a
 // request, one per lane. Per chunk of 16 outputs the warp stages its 32 x 16 tile and lane 0
 // writes it with one 2D tensor store through the request's map (columns past per_stream are
-// clipped). fp carries the request's reject rule.
-template <int W, int FORM, int MAP, uint32_t CVT>
+// clipped). With CH = 32 each lane makes 32 outputs per chunk while 32 remain, written as two
+// stores of the two sub-tiles, and the rest of the row in chunks of 16. fp carries the
+// request's reject rule.
+// A shifted request (rows starting 16 bytes into a 32-byte sector) would have every store begin
+// and end in half a sector. Its map instead starts 2 outputs into each row (16 bytes further,
+// on a sector boundary, with the rows' own pitch) and covers outputs 2 .. per_stream - 1: each
+// lane keeps its row's first two outputs in registers and writes them as one 16-byte store
+// after the row, when the lane below writes the other half of that sector (its row's last two
+// outputs).
+template <int W, int FORM, int MAP, uint32_t CVT, int CH = kChunk>
 __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp, const CUtensorMap* map,
                                                 uint64_t row0, const BatchParams& bp, const FillParams& fp,
                                                 uint32_t tile, int lane) {
@@ -168,9 +197,32 @@ __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp
   const uint32_t sw = (uint32_t)(lane & 7);
   if (lane == 0)  // the map was rewritten by a host copy since an earlier batch may have used this slot
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
-  const uint32_t per = (uint32_t)dp->per_stream;
+  const bool shift = dp->shift != 0;  // warp-uniform
+  uint64_t head0 = 0, head1 = 0;
+  if (shift) {
+    const RowHead rh = row_head<W, FORM, MAP>(RowState{st, rej}, bp, fp.single);
+    st = rh.rs.st;
+    rej = rh.rs.rej;
+    head0 = rh.v0;
+    head1 = rh.v1;
+  }
+  const uint32_t per = (uint32_t)dp->per_stream - (shift ? 2u : 0u);  // outputs the map covers
+  uint32_t x0 = 0;
+  if constexpr (CH == 2 * kChunk) {
 #pragma unroll 1
-  for (uint32_t x0 = 0; x0 < per; x0 += kChunk) {
+    for (; per - x0 >= (uint32_t)CH; x0 += CH) {
+      stage_full_chunk<W, FORM, MAP, CVT, CH>(st, rej, fp, my_row, sw, lane);
+      fence_async_shared();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d_global_map(map, tile, (int)x0, (int)row0);
+        tma_store_2d_global_map(map, tile + (uint32_t)kTileBytes, (int)(x0 + kChunk), (int)row0);
+        bulk_commit();
+      }
+    }
+  }
+#pragma unroll 1
+  for (; x0 < per; x0 += kChunk) {
     const uint32_t left = per - x0;
     if (left >= (uint32_t)kChunk) {
       stage_full_chunk<W, FORM, MAP, CVT>(st, rej, fp, my_row, sw, lane);
@@ -185,6 +237,10 @@ __device__ __forceinline__ void batch_item_full(const BatchDesc* __restrict__ dp
       tma_store_2d_global_map(map, tile, (int)x0, (int)row0);
       bulk_commit();
     }
+  }
+  if (shift) {
+    ulonglong2* head = (ulonglong2*)(dp->out + row * dp->per_stream);  // 16-byte aligned
+    *head = make_ulonglong2(head0, head1);
   }
   if (dp->resident) bp.state[dp->first_stream + row] = make_uint4(st.x, st.y, st.z, st.w);
   uint64_t* rejects = dp->rejects;
@@ -251,11 +307,11 @@ __device__ __noinline__ void batch_item_ragged(const BatchDesc* __restrict__ dp,
 }
 
 // fp: the launch's constants for MAP with the request's reject rule; CVT as for stage_full_chunk.
-template <int W, int FORM, int MAP = 0, uint32_t CVT = cvt_group_mask<FORM, W, MAP>()>
+template <int W, int FORM, int MAP = 0, uint32_t CVT = cvt_group_mask<FORM, W, MAP>(), int CH = kChunk>
 __device__ __forceinline__ void batch_item(const BatchDesc* __restrict__ dp, const CUtensorMap* map, uint64_t row0,
                                            const BatchParams& bp, const FillParams& fp, uint32_t tile, int lane) {
   if (row0 + 32 <= dp->full_rows)  // warp-uniform
-    batch_item_full<W, FORM, MAP, CVT>(dp, map, row0, bp, fp, tile, lane);
+    batch_item_full<W, FORM, MAP, CVT, CH>(dp, map, row0, bp, fp, tile, lane);
   else
     batch_item_ragged<W, FORM, MAP>(dp, row0, bp, tile, lane);
 }
@@ -313,15 +369,18 @@ constexpr int kFormBBalanced = 3;
 constexpr int kMixA = kFormAF;
 constexpr uint32_t kMixCvtB = 0u, kMixCvtC = 0u;
 
-template <int W, int FORM_ALL>
+// CH: outputs per lane per staged chunk of full items (kChunk, or 2 kChunk in two sub-tiles);
+// the any-mode kernel and ragged items stage kChunk at a time.
+template <int W, int FORM_ALL, int CH = kChunk>
 __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ BatchParams bp) {
+  constexpr uint32_t kWarpTile = (uint32_t)CH * 32u * 8u;
   extern __shared__ uint8_t smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
   const uint32_t n_req = bp.meta[0];
   const uint32_t pad = (1024u - (smem_addr(smem_raw) & 1023u)) & 1023u;  // tiles 1024-byte aligned (swizzle)
-  const uint32_t tile = smem_addr(smem_raw) + pad + (uint32_t)warp * kTileBytes;
-  uint32_t* prefix = (uint32_t*)(smem_raw + pad + (size_t)warps * kTileBytes);
+  const uint32_t tile = smem_addr(smem_raw) + pad + (uint32_t)warp * kWarpTile;
+  uint32_t* prefix = (uint32_t*)(smem_raw + pad + (size_t)warps * kWarpTile);
   for (uint32_t i = threadIdx.x; i <= n_req; i += blockDim.x) prefix[i] = bp.meta[1 + i];
   __syncthreads();
   const uint32_t total = prefix[n_req];
@@ -353,14 +412,17 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
           default: batch_item_form_any_map<W, kFormB>(dp, bp.maps + r, row0, bp, tile, lane); break;
         }
       } else if constexpr (FORM_ALL == kFormBBalanced) {
-        batch_item<W, kFormB, kMapCvt>(dp, bp.maps + r, row0, bp, fp, tile, lane);
+        batch_item<W, kFormB, kMapCvt, cvt_group_mask<kFormB, W, kMapCvt>(), CH>(dp, bp.maps + r, row0, bp, fp, tile,
+                                                                                lane);
       } else if constexpr (FORM_ALL >= 0) {
-        batch_item<W, FORM_ALL>(dp, bp.maps + r, row0, bp, fp, tile, lane);
+        batch_item<W, FORM_ALL, 0, cvt_group_mask<FORM_ALL, W, 0>(), CH>(dp, bp.maps + r, row0, bp, fp, tile, lane);
       } else {
         switch (dp->form) {
-          case kFormA: batch_item<W, kMixA>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
-          case kFormC: batch_item<W, kFormC, 0, kMixCvtC>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
-          default: batch_item<W, kFormB, 0, kMixCvtB>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          case kFormA:
+            batch_item<W, kMixA, 0, cvt_group_mask<kMixA, W, 0>(), CH>(dp, bp.maps + r, row0, bp, fp, tile, lane);
+            break;
+          case kFormC: batch_item<W, kFormC, 0, kMixCvtC, CH>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
+          default: batch_item<W, kFormB, 0, kMixCvtB, CH>(dp, bp.maps + r, row0, bp, fp, tile, lane); break;
         }
       }
     }
@@ -368,14 +430,15 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
   if (lane == 0) bulk_wait_all();
 }
 
-// Host: one launch of batch_kernel<W, FORM_ALL>, `blocks` blocks of `warps` warps; the
+// Host: one launch of batch_kernel<W, FORM_ALL, CH>, `blocks` blocks of `warps` warps; the
 // dynamic shared memory holds the warps' tiles and the item prefix of up to max_req requests.
-template <int W, int FORM_ALL>
+template <int W, int FORM_ALL, int CH = kChunk>
 cudaError_t launch_batch_kernel(const BatchParams& p, int warps, unsigned blocks, int max_req, cudaStream_t s) {
-  auto k = batch_kernel<W, FORM_ALL>;
-  const size_t smem = 1024 + (size_t)warps * kTileBytes + 4 * ((size_t)max_req + 1);
-  static std::atomic<uint64_t> attr{0};
-  const cudaError_t e = prngd::smem_limit_once(k, 64 * 1024, attr);
+  auto k = batch_kernel<W, FORM_ALL, CH>;
+  const size_t tile = (size_t)CH * 32 * 8;
+  const size_t smem = 1024 + (size_t)warps * tile + 4 * ((size_t)max_req + 1);
+  static std::atomic<uint64_t> attr{0};  // the largest launch: 8 warps, 4096 requests
+  const cudaError_t e = prngd::smem_limit_once(k, (int)(1024 + 8 * tile + 4 * (4096 + 1)), attr);
   if (e != cudaSuccess) return e;
   k<<<blocks, warps * 32, smem, s>>>(p);
   return cudaGetLastError();

@@ -132,12 +132,36 @@ def test_result_is_the_same_alone_and_in_a_mix_and_for_any_launch_shape():
             P.prng_wait(g.h, P.prng_submit(g.h, reqs), 60)
             return as_host(b, target["L"], target["form"])
 
-        alone = run_target(0, (8, 4, 1))
-        mixed = run_target(200, (8, 4, 1))
-        other = run_target(200, (1, 1, 5))
         want, _ = oracle_fresh(77, 123, 30011, 0, 32, P.FORM_B_INTBITS)
-        assert same(alone, want) and same(mixed, want) and same(other, want)
-        P.prng_batch_set_shape(g.h, 8, 4, 1)
+        # every tuned dimension: warps per block, blocks per SM, items per ticket, outputs per chunk
+        for extra, shape in [(0, (8, 4, 1, 16)), (200, (8, 4, 1, 16)), (200, (1, 1, 5, 16)), (0, (8, 3, 4, 32)),
+                             (200, (4, 2, 8, 32)), (200, (1, 1, 1, 32))]:
+            assert same(run_target(extra, shape), want), (extra, shape)
+        P.prng_batch_set_shape(g.h, 8, 4, 1, 16)
+
+
+@pytest.mark.parametrize("form", [P.FORM_A_FP64, P.FORM_B_INTBITS, P.FORM_C_F32PAIR])
+def test_outputs_per_chunk_32_rows_of_every_length(form):
+    """Rows whose lengths leave every remainder after chunks of 32 (a whole number, 16 + k, k < 16)
+    through the 32-output staging: each matches the oracle, in a mode-0 batch of one form and in
+    the mixed-form batch."""
+    with P.Generator(3, 64, 32) as g:
+        P.prng_batch_set_shape(g.h, 8, 3, 4, 32)
+        chunks = [64, 96, 80, 82, 94, 32, 48, 18, 1024, 1040, 1058]
+        for mixed in (False, True):
+            bufs, reqs = [], []
+            for i, ch in enumerate(chunks):
+                L = ch * 40 + (7 if i % 3 == 0 else 0)  # whole items of 32 rows, and a ragged tail
+                b = dev_buf(L)
+                bufs.append((b, L, ch))
+                f = form if not mixed else (form, (form + 1) % 3)[i % 2]
+                reqs.append(P.fresh_request(b, L, 500 + i, 1000 * i, f, ch))
+            P.prng_wait(g.h, P.prng_submit(g.h, reqs), 60)
+            for i, (b, L, ch) in enumerate(bufs):
+                f = form if not mixed else (form, (form + 1) % 3)[i % 2]
+                want, _ = oracle_fresh(500 + i, 1000 * i, L, ch, 32, f)
+                assert same(as_host(b, L, f), want), (mixed, ch, f)
+        P.prng_batch_set_shape(g.h, 8, 3, 4, 16)
 
 
 def test_batch_errors():
@@ -185,7 +209,9 @@ def test_autotune_table_roundtrip(tmp_path):
     with P.Generator(1, 1, 32) as g:
         best = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, 2**14, path)
         assert best["ms"] > 0 and 1 <= best["warps_per_block"] <= 8
-        assert P.prng_batch_get_shape(g.h) == (best["warps_per_block"], best["blocks_per_sm"], best["items_per_ticket"])
+        assert best["outputs_per_chunk"] in (16, 32)
+        assert P.prng_batch_get_shape(g.h) == (best["warps_per_block"], best["blocks_per_sm"], best["items_per_ticket"],
+                                               best["outputs_per_chunk"])
         again = P.prng_batch_autotune(g.h, P.FORM_B_INTBITS, 2**8, 2**14, path)  # read back, no timing
         assert again["ms"] == -1 and again["warps_per_block"] == best["warps_per_block"]
         b = dev_buf(5001)
@@ -245,3 +271,41 @@ def test_bounded_waits_report_timeouts_and_recover():
             assert all(P.prng_server_poll(srv, i)[0] for i in ids)
         finally:
             P.prng_server_destroy(srv)
+
+
+@pytest.mark.parametrize("chunk_depth", [16, 32])
+@pytest.mark.parametrize("forms", [(P.FORM_B_INTBITS,), (P.FORM_C_F32PAIR,), (P.FORM_A_FP64, P.FORM_B_INTBITS,
+                                                                              P.FORM_C_F32PAIR)])
+def test_requests_16_bytes_into_a_sector(forms, chunk_depth):
+    """Outputs that start 16 bytes into a 32-byte sector: rows of a multiple of 4 outputs take the
+    shifted map (the row's first two outputs written after the row); others keep the plain map.
+    Every value, reject count and the guard words on both sides of each request are checked."""
+    sentinel = -7.0
+    with P.Generator(21, 2048, 32) as g:
+        P.prng_batch_set_shape(g.h, 8, 3, 4, chunk_depth)
+        cases = [(1024, 40 * 1024), (64, 64 * 35 + 17), (100, 100 * 33), (36, 36 * 70 + 2), (20, 20 * 64),
+                 (1026, 1026 * 33), (18, 18 * 40), (4, 4 * 40), (1040, 1040 * 32 + 1000)]
+        reqs, bufs = [], []
+        for i, (chunk, L) in enumerate(cases):
+            pool = torch.full((L + 8,), sentinel, dtype=torch.float64, device="cuda")  # 256-byte aligned
+            b = pool[2:]  # 16 bytes into a sector
+            form = forms[i % len(forms)]
+            rej = torch.zeros((L + chunk - 1) // chunk, dtype=torch.int64, device="cuda")
+            reqs.append(P.fresh_request(b, L, 300 + i, 5000 * i, form, chunk, rej))
+            bufs.append((pool, rej, chunk, L, form))
+        # a resident request at the same offset (rows of a multiple of 16 outputs)
+        rpool = torch.full((64 * 96 + 8,), sentinel, dtype=torch.float64, device="cuda")
+        rrej = torch.zeros(64, dtype=torch.int64, device="cuda")
+        reqs.append(P.resident_request(rpool[2:], 64 * 96, 100, 64, forms[0], rrej))
+        P.prng_wait(g.h, P.prng_submit(g.h, reqs), 60)
+        for i, (pool, rej, chunk, L, form) in enumerate(bufs):
+            wv, wr = oracle_fresh(300 + i, 5000 * i, L, chunk, 32, form)
+            assert same(as_host(pool[2:], L, form), wv), (chunk, L, form)
+            assert np.array_equal(rej.cpu().numpy().astype(np.uint64), wr)
+            guard = torch.cat([pool[:2], pool[2 + L:]]).cpu().numpy()
+            assert (guard == sentinel).all(), (chunk, L)
+        wv, wr, _ = oracle_resident([O.stream_seed(21, s) for s in range(100, 164)], 64 * 96, 32, forms[0])
+        assert same(as_host(rpool[2:], 64 * 96, forms[0]), wv)
+        assert np.array_equal(rrej.cpu().numpy().astype(np.uint64), wr)
+        assert (torch.cat([rpool[:2], rpool[2 + 64 * 96:]]).cpu().numpy() == sentinel).all()
+        P.prng_batch_set_shape(g.h, 8, 3, 4, 16)

@@ -190,6 +190,7 @@ def test_mode_is_independent_of_the_batch_and_shape():
         assert same(run(0, (8, 3, 4)), want)
         assert same(run(100, (8, 3, 4)), want)
         assert same(run(100, (2, 1, 1)), want)
+        assert same(run(100, (8, 3, 4, 32)), want)  # the any-mode kernel stages 16 outputs whatever the shape
         P.prng_batch_set_shape(g.h, 8, 3, 4)
 
 
