@@ -627,9 +627,17 @@ def served(torch, P, plain_rate, seconds, mix_rate=None):
         g.close()
     rate = total / makespan / 1e9
     sat_rate = sat_total / sat_makespan / 1e9
+    lat = np.asarray(lat)
+    length = np.array([r["length"] for r in trace])  # the server's lanes by request length
+    classes = (("le_2p20", length <= 2**20), ("2p20_to_2p24", (length > 2**20) & (length <= 2**24)),
+               ("gt_2p24", length > 2**24))
+    lanes = {name: {"requests": int(m.sum()), "p50_ms": float(np.percentile(lat[m], 50) * 1e3),
+                    "p99_ms": float(np.percentile(lat[m], 99) * 1e3)}
+             for name, m in classes if m.any()}
     return {"requests": len(trace), "outputs": total, "offered_gsamples_s": total / seconds / 1e9,
             "gsamples_s": rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "makespan_s": makespan, "batches": info["batches"],
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "by_lane": lanes,
+            "makespan_s": makespan, "batches": info["batches"],
             "saturation_gsamples_s": sat_rate, "saturation_vs_plain_fill": sat_rate / plain_rate,
             "plain_fill_of_form_mix_gsamples_s": mix_rate,
             "saturation_vs_plain_fill_of_form_mix": (sat_rate / mix_rate) if mix_rate else None,

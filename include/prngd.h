@@ -336,7 +336,7 @@ typedef struct prng_request {
  * Resident requests of one batch must not share streams; batches on different CUDA streams
  * that use the same resident streams must be ordered by the caller.
  * Errors: PRNG_EINVAL (bad request, overlapping resident ranges, n out of range),
- * PRNG_EBUSY (all 16 batch slots still in flight: poll or wait, then retry), PRNG_ENOMEM,
+ * PRNG_EBUSY (all 32 batch slots still in flight: poll or wait, then retry), PRNG_ENOMEM,
  * PRNG_ECUDA.
  */
 int prng_submit(prng_t h, const prng_request* reqs, int n, uint64_t* ticket, void* cuda_stream);
@@ -393,9 +393,12 @@ int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_
  * Admission: prng_server_submit takes output memory from a device pool of pool_bytes
  * (allocated once by prng_server_create) and returns PRNG_EBUSY when it does not fit;
  * the caller retries after releasing finished requests.
- * Batching: prng_server_step harvests finished batches and launches every admitted request
- * whose client is idle as one batch (small and large requests on two CUDA streams), so work
- * admitted while other batches run overlaps with them on the device.
+ * Batching: prng_server_step harvests finished batches and launches the admitted requests of
+ * idle clients as batches, one per lane: requests of up to 2^20 outputs, up to 2^24, and
+ * longer. Up to 8 batches of a lane are on the device at once, each on a CUDA stream of its
+ * own (lanes of shorter requests at higher stream priority), so work admitted while other
+ * batches run overlaps with them. The server's batches take one item (32 rows) per warp and
+ * then end their blocks, which frees SM slots item by item for the other lanes.
  * Results stay in the pool until prng_server_release; prng_server_poll gives the device
  * pointer, prng_server_read copies them to the host.
  * A server is not thread-safe. Errors as for the batch calls; PRNG_ENOTFOUND for an unknown
@@ -427,8 +430,9 @@ int prng_server_info(prng_server_t s, uint64_t* n_clients, uint64_t* batches, ui
 
 /*
  * prng_server_run_trace -- replay an arrival trace in real time: item i arrives t seconds
- * after the call starts (items sorted by t), is admitted in arrival order when the pool has
- * room, runs, and is released as soon as it finishes. latency (nullable, n doubles) gets
+ * after the call starts (items sorted by t), is admitted when the pool has room (in arrival
+ * order within each lane, and always after its client's earlier arrivals, so a small request
+ * does not wait for the memory of a large one), runs, and is released as soon as it finishes. latency (nullable, n doubles) gets
  * finish time minus arrival time per item; makespan (nullable) the total wall time.
  * Errors: PRNG_ETIMEOUT after timeout_s seconds, and those of the calls above.
  */

@@ -19,7 +19,7 @@
 
 namespace prngd_host {
 
-static constexpr int kSlots = 16;
+static constexpr int kSlots = 32;
 
 struct BatchSlot {
   prngd::BatchDesc* h_desc = nullptr;  // pinned
@@ -103,30 +103,32 @@ BatchShape default_batch_shape(int num_sms) {
 }
 
 template <int W, int FORM_ALL>
-static cudaError_t launch_batch_wf(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s) {
-  const unsigned blocks = (unsigned)(num_sms * sh.blocks_per_sm);
+static cudaError_t launch_batch_wf(const prngd::BatchParams& p, const BatchShape& sh, unsigned blocks, int max_req,
+                                   cudaStream_t s) {
   if (sh.outputs_per_chunk == 2 * prngd::kChunk)
-    return prngd::launch_batch_kernel<W, FORM_ALL, 2 * prngd::kChunk>(p, sh.warps_per_block, blocks,
-                                                                      PRNG_MAX_BATCH_REQUESTS, s);
-  return prngd::launch_batch_kernel<W, FORM_ALL>(p, sh.warps_per_block, blocks, PRNG_MAX_BATCH_REQUESTS, s);
+    return prngd::launch_batch_kernel<W, FORM_ALL, 2 * prngd::kChunk>(p, sh.warps_per_block, blocks, max_req, s);
+  return prngd::launch_batch_kernel<W, FORM_ALL>(p, sh.warps_per_block, blocks, max_req, s);
 }
 
 template <int W>
-static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, int form_all,
-                                  cudaStream_t s) {
+static cudaError_t launch_batch_w(const prngd::BatchParams& p, const BatchShape& sh, unsigned blocks, int max_req,
+                                  int form_all, cudaStream_t s) {
   switch (form_all) {
-    case prngd::kAnyMode: return launch_batch_any_mode_w<W>(p, sh, num_sms, s);
-    case prngd::kFormBBalanced: return launch_batch_wf<W, prngd::kFormBBalanced>(p, sh, num_sms, s);
-    case prngd::kFormA: return launch_batch_wf<W, prngd::kFormA>(p, sh, num_sms, s);
-    case prngd::kFormB: return launch_batch_wf<W, prngd::kFormB>(p, sh, num_sms, s);
-    case prngd::kFormC: return launch_batch_wf<W, prngd::kFormC>(p, sh, num_sms, s);
-    default: return launch_batch_wf<W, -1>(p, sh, num_sms, s);
+    case prngd::kAnyMode: return launch_batch_any_mode_w<W>(p, sh, blocks, max_req, s);
+    case prngd::kFormBBalanced: return launch_batch_wf<W, prngd::kFormBBalanced>(p, sh, blocks, max_req, s);
+    case prngd::kFormA: return launch_batch_wf<W, prngd::kFormA>(p, sh, blocks, max_req, s);
+    case prngd::kFormB: return launch_batch_wf<W, prngd::kFormB>(p, sh, blocks, max_req, s);
+    case prngd::kFormC: return launch_batch_wf<W, prngd::kFormC>(p, sh, blocks, max_req, s);
+    default: return launch_batch_wf<W, -1>(p, sh, blocks, max_req, s);
   }
 }
 
-// The captured part of a launch: reset the item counter, run the persistent kernel. The
-// descriptors and item prefix are copied before it (sized to the batch) by submit().
-static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaStream_t s) {
+// A launch: reset the item counter, run the kernel. The descriptors and item prefix are
+// copied before it (sized to the batch) by submit(). A graph captures it with the persistent
+// grid (blocks = 0: the shape's blocks per SM on every SM, shared memory for the largest
+// batch); a capped launch passes its own grid and request count.
+static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaStream_t s, unsigned blocks = 0,
+                                 int max_req = PRNG_MAX_BATCH_REQUESTS, uint32_t items_per_warp = 0, int warps = 0) {
   BatchEngine* b = h->batch;
   prngd::BatchParams p;
   p.desc = sl.d_desc;
@@ -139,6 +141,8 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaS
   p.w = h->w;
   p.one = 1;
   p.items_per_ticket = (uint32_t)b->shape.items_per_ticket;
+  p.items_per_warp = items_per_warp;
+  if (!blocks) blocks = (unsigned)(h->num_sms * b->shape.blocks_per_sm);
   prngd::FillParams f4, f5;  // the map constants (Eq. 5 division, form A and form L factors)
   set_mode_constants(f4, h->w, 0);
   set_mode_constants(f5, h->w, PRNG_MODE_EQ5);
@@ -151,9 +155,11 @@ static cudaError_t enqueue_batch(prng_ctx* h, BatchSlot& sl, int form_all, cudaS
   p.l2_eq5 = f5.l2;
   cudaError_t e = cudaMemsetAsync(sl.d_ticket, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  if (h->w == 32) return launch_batch_w<32>(p, b->shape, h->num_sms, form_all, s);
-  if (h->w == 24) return launch_batch_w<24>(p, b->shape, h->num_sms, form_all, s);
-  return launch_batch_w<0>(p, b->shape, h->num_sms, form_all, s);
+  BatchShape sh = b->shape;
+  if (warps) sh.warps_per_block = warps;
+  if (h->w == 32) return launch_batch_w<32>(p, sh, blocks, max_req, form_all, s);
+  if (h->w == 24) return launch_batch_w<24>(p, sh, blocks, max_req, form_all, s);
+  return launch_batch_w<0>(p, sh, blocks, max_req, form_all, s);
 }
 
 // Capture the slot's reset + launch once per launch shape.
@@ -230,6 +236,11 @@ static int describe(prng_ctx* h, const prng_request& r, prngd::BatchDesc& d) {
 }
 
 int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaStream_t s) {
+  return submit_capped(h, reqs, n, ticket, s, 0);
+}
+
+int submit_capped(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaStream_t s,
+                  uint32_t items_per_warp, int warps) {
   if (n <= 0 || n > PRNG_MAX_BATCH_REQUESTS)
     return fail(PRNG_EINVAL, "a batch holds 1 .. %d requests", PRNG_MAX_BATCH_REQUESTS);
   std::vector<prngd::BatchDesc> d(n);
@@ -293,14 +304,25 @@ int submit(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaS
   for (int i = 0; i < n; ++i)
     if (d[i].mode || d[i].form == PRNG_FORM_L_ALGO1) form_all = prngd::kAnyMode;
   if (all_b_round) form_all = prngd::kFormBBalanced;
-  rc = ensure_graph(h, *sl, form_all);
-  if (rc) return rc;
+  if (!items_per_warp) {
+    rc = ensure_graph(h, *sl, form_all);
+    if (rc) return rc;
+  }
   cudaError_t e = cudaMemcpyAsync(sl->d_desc, sl->h_desc, sizeof(prngd::BatchDesc) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl->d_maps, sl->h_maps, sizeof(CUtensorMap) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(sl->d_meta, sl->h_meta, sizeof(uint32_t) * (n + 2), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaGraphLaunch(sl->exec[form_all + 2], s);
+  if (e == cudaSuccess) {
+    if (items_per_warp) {
+      const int wpb = (warps >= 1 && warps <= 8) ? warps : b->shape.warps_per_block;
+      const uint64_t per_block = (uint64_t)wpb * items_per_warp;
+      const uint64_t blocks = (acc + per_block - 1) / per_block;
+      e = enqueue_batch(h, *sl, form_all, s, (unsigned)std::max<uint64_t>(1, blocks), n, items_per_warp, wpb);
+    } else {
+      e = cudaGraphLaunch(sl->exec[form_all + 2], s);
+    }
+  }
   if (e == cudaSuccess) e = cudaEventRecord(sl->done, s);
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "batch launch: %s", cudaGetErrorString(e));
   sl->ticket = b->next_ticket++;

@@ -47,6 +47,8 @@ struct BatchParams {
   int w;
   uint32_t one;
   uint32_t items_per_ticket;
+  uint32_t items_per_warp;        // 0: a warp takes items until none is left; else it stops
+                                  // after taking at least this many (the grid covers the batch)
   DivConst ec;                    // Eq. 5: constants of D - 2
   double scale5;                  // Eq. 5, form A: RN((1 - k^2)/(D - 2))
   double k;                       // form L: 2^-w and its folded constants under Eq. 4 and Eq. 6
@@ -386,12 +388,15 @@ __global__ void __launch_bounds__(256, 3) batch_kernel(const __grid_constant__ B
   const uint32_t total = prefix[n_req];
   const FillParams fp = fill_params_of(bp);
   uint32_t r = 0;
+  uint32_t taken = 0;
   for (;;) {
+    if (bp.items_per_warp && taken >= bp.items_per_warp) break;  // warp-uniform
     unsigned long long first = 0;
     if (lane == 0) first = atomicAdd(bp.ticket, (unsigned long long)bp.items_per_ticket);
     first = __shfl_sync(0xffffffffu, first, 0);
     if (first >= total) break;
     const uint32_t last = (uint32_t)(first + bp.items_per_ticket < total ? first + bp.items_per_ticket : total);
+    taken += last - (uint32_t)first;
 #pragma unroll 1
     for (uint32_t item = (uint32_t)first; item < last; ++item) {
       if (item < prefix[r] || item >= prefix[r + 1]) {  // largest r with prefix[r] <= item

@@ -17,9 +17,8 @@ namespace prngd_host {
 
 template <>
 cudaError_t launch_batch_any_mode_w<PRNGD_ANY_MODE_W>(const prngd::BatchParams& p, const BatchShape& sh,
-                                                       int num_sms, cudaStream_t s) {
-  return prngd::launch_batch_kernel<PRNGD_ANY_MODE_W, prngd::kAnyMode>(
-      p, sh.warps_per_block, (unsigned)(num_sms * sh.blocks_per_sm), PRNG_MAX_BATCH_REQUESTS, s);
+                                                       unsigned blocks, int max_req, cudaStream_t s) {
+  return prngd::launch_batch_kernel<PRNGD_ANY_MODE_W, prngd::kAnyMode>(p, sh.warps_per_block, blocks, max_req, s);
 }
 
 }  // namespace prngd_host

@@ -94,14 +94,23 @@ void release_batch(prng_ctx* h);
 BatchShape default_batch_shape(int num_sms);
 // The batch kernel for requests of any form and mode at w = W (32, 24, or 0 for the generic
 // code); one translation unit defines each.
+// `blocks` blocks of the shape's warps, shared memory for the item prefix of max_req requests.
 template <int W>
-cudaError_t launch_batch_any_mode_w(const prngd::BatchParams& p, const BatchShape& sh, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_any_mode_w(const prngd::BatchParams& p, const BatchShape& sh, unsigned blocks, int max_req,
+                                    cudaStream_t s);
 template <>
-cudaError_t launch_batch_any_mode_w<32>(const prngd::BatchParams&, const BatchShape&, int, cudaStream_t);
+cudaError_t launch_batch_any_mode_w<32>(const prngd::BatchParams&, const BatchShape&, unsigned, int, cudaStream_t);
 template <>
-cudaError_t launch_batch_any_mode_w<24>(const prngd::BatchParams&, const BatchShape&, int, cudaStream_t);
+cudaError_t launch_batch_any_mode_w<24>(const prngd::BatchParams&, const BatchShape&, unsigned, int, cudaStream_t);
 template <>
-cudaError_t launch_batch_any_mode_w<0>(const prngd::BatchParams&, const BatchShape&, int, cudaStream_t);
+cudaError_t launch_batch_any_mode_w<0>(const prngd::BatchParams&, const BatchShape&, unsigned, int, cudaStream_t);
+// prng_submit with an optional cap on the items each warp takes (items_per_warp > 0): the batch
+// is then launched directly (no graph) with just enough blocks to cover its items under the
+// cap, so that its blocks finish, and free their SM slots, every few items instead of at the
+// end of the batch. The serving loop uses it; 0 is prng_submit.
+// warps (> 0) overrides the shape's warps per block for a capped launch.
+int submit_capped(prng_ctx* h, const prng_request* reqs, int n, uint64_t* ticket, cudaStream_t s,
+                  uint32_t items_per_warp, int warps = 0);
 int set_batch_shape(prng_ctx* h, const BatchShape& sh);
 int get_batch_shape(prng_ctx* h, BatchShape* sh);
 }  // namespace prngd_host

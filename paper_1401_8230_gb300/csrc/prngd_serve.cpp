@@ -7,14 +7,15 @@
 // and the request itself, never by what else is in flight. A client has at most one request
 // on the device at a time; later requests of a busy client wait in order.
 //
-// Batching: step() puts every admitted request whose client is idle into the next batch
-// (small and large requests go to two separate lanes, so small requests do not wait behind
-// large ones) and harvests finished batches. Requests that arrive while batches run are
-// admitted as soon as pool memory allows and join the next batch. Within a lane, successive
-// batches rotate over several CUDA streams: no two batches in flight share a client (hence
-// a stream of the handle), so they need no order, and a batch whose last long rows are still
-// running no longer holds the next one back (a 2^28-output request of a 16384-stream client
-// has rows of 16384 outputs, a few milliseconds of one warp's work).
+// Batching: step() puts every admitted request whose client is idle into the next batch of
+// its lane (three lanes by request length, so that a request is not held back by much longer
+// batch-mates) and harvests finished batches. Requests that arrive while batches run are
+// admitted as soon as pool memory allows and join the next batch. Every batch in flight has a
+// CUDA stream of its own: no two batches in flight share a client (hence a stream of the
+// handle), so they need no order, and a batch does not wait for another to finish (a 2^28-output
+// request of a 16384-stream client has rows of 16384 outputs, a few milliseconds of one warp's
+// work). Batches are launched with a cap of one item per warp, so their blocks free SM slots
+// item by item, and the lanes of shorter requests run on streams of higher priority.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -70,10 +71,44 @@ struct Req {
   double t_admit, t_done;
 };
 
-constexpr int kLanes = 2;                      // small / large requests
-constexpr int kStreamsPerLane = 3;             // CUDA streams a lane's batches rotate over
-constexpr int kMaxBatchesPerLane = 6;          // batches of one lane on the device at once
-constexpr uint64_t kLargeOutputs = 1ull << 20;  // requests above this go to the large lane
+// Lanes by request size: small (<= 2^20 outputs), medium (<= 2^24), large. A batch finishes as
+// a whole, so a request batched with much longer ones would wait for them; separate lanes keep
+// a request's batch-mates of a similar length.
+#ifndef PRNGD_SERVE_LANES
+#define PRNGD_SERVE_LANES 3
+#endif
+constexpr int kLanes = PRNGD_SERVE_LANES;
+constexpr uint64_t kLaneMax[3] = {1ull << 20, kLanes == 3 ? 1ull << 24 : ~0ull, ~0ull};  // longest request of a lane
+#ifndef PRNGD_SERVE_STREAMS
+#define PRNGD_SERVE_STREAMS 8
+#endif
+#ifndef PRNGD_SERVE_WARPS
+#define PRNGD_SERVE_WARPS 4
+#endif
+// Batches of one lane on the device at once, each on a CUDA stream of its own: a batch that
+// shared a stream waited for the one before it (small batches: 0.36 ms on the GPU at the
+// median, 1.2 ms from launch to completion with 6 batches over 3 streams).
+constexpr int kStreamsPerLane = PRNGD_SERVE_STREAMS;
+constexpr int kMaxBatchesPerLane = PRNGD_SERVE_STREAMS;
+// Warps per block of the serving launches (0: the handle's shape). With 4 a slot frees up when
+// 4 items end rather than 8: measured p50 / p99 0.61 / 10.4 ms and saturation 554 Gsamples/s,
+// against 0.56 / 10.6 ms and 530 with the shape's 8.
+constexpr int kServeWarps = PRNGD_SERVE_WARPS;
+#ifndef PRNGD_SERVE_CAP
+#define PRNGD_SERVE_CAP 1
+#endif
+// Items (32 rows of a request) each warp of a lane's batch takes before its block ends (0: the
+// persistent launch of prng_submit). A persistent batch holds its SM slots until its last
+// item, and an item of a 2^28-output request is milliseconds of one warp's work, so small
+// requests waited for whole large batches; with capped batches slots free up every item and go
+// first to the lanes of shorter requests, whose streams have higher priority.
+constexpr uint32_t kLaneCap = PRNGD_SERVE_CAP;
+
+int lane_of(uint64_t length) {
+  int l = 0;
+  while (l < kLanes - 1 && length > kLaneMax[l]) ++l;
+  return l;
+}
 
 }  // namespace
 
@@ -158,7 +193,10 @@ int launch_lane(prng_server* s, int lane) {
   s->waiting[lane] = std::move(keep);
   if (batch.empty()) return PRNG_OK;
   uint64_t ticket = 0;
-  int rc = prng_submit(s->h, batch.data(), (int)batch.size(), &ticket, s->lane_stream[lane][s->lane_next[lane]]);
+  int rc = prngd_host::check_handle_device(s->h);
+  if (rc) return rc;
+  rc = prngd_host::submit_capped(s->h, batch.data(), (int)batch.size(), &ticket,
+                                 s->lane_stream[lane][s->lane_next[lane]], kLaneCap, kServeWarps);
   if (rc == PRNG_EBUSY) {  // no free batch slot: put them back in front, in order
     for (size_t i = ids.size(); i-- > 0;) s->waiting[lane].push_front(ids[i]);
     return PRNG_OK;
@@ -206,9 +244,15 @@ int prng_server_create(prng_server_t* out, prng_t h, uint64_t streams_per_client
     delete s;
     return fail(PRNG_ENOMEM, "output pool of %zu bytes", pool_bytes);
   }
+  int least = 0, greatest = 0;  // numerically lower is higher priority
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+    cudaGetLastError();
+    least = greatest = 0;
+  }
   for (int l = 0; l < kLanes; ++l)
     for (int k = 0; k < kStreamsPerLane; ++k)
-      if (cudaStreamCreateWithFlags(&s->lane_stream[l][k], cudaStreamNonBlocking) != cudaSuccess) {
+      if (cudaStreamCreateWithPriority(&s->lane_stream[l][k], cudaStreamNonBlocking,
+                                       std::min(least, greatest + l)) != cudaSuccess) {  // lane 0 highest
         cudaGetLastError();
         for (auto& lane : s->lane_stream)
           for (auto& st : lane)
@@ -262,7 +306,7 @@ int prng_server_submit_mode(prng_server_t s, uint64_t client, uint64_t length, i
   r.t_done = 0;
   *id = s->next_id++;
   s->reqs[*id] = r;
-  s->waiting[length > kLargeOutputs ? 1 : 0].push_back(*id);
+  s->waiting[lane_of(length)].push_back(*id);
   s->client_q[client].push_back(*id);
   return PRNG_OK;
 }
@@ -347,24 +391,50 @@ int prng_server_run_trace(prng_server_t s, const prng_trace_item* items, uint64_
                           double* makespan, double timeout_s) {
   if (!s || (!items && n)) return fail(PRNG_EINVAL, "null argument");
   const double t_start = s->now();
-  std::deque<uint64_t> arrived;              // indices waiting for pool memory
+  // Arrivals waiting for pool memory, per lane: a small request does not wait behind a large
+  // one refused for memory. A request is admitted only as its client's earliest waiting
+  // arrival, so every client's requests are admitted (and run) in arrival order.
+  std::deque<uint64_t> arrived[kLanes];
+  std::unordered_map<uint64_t, std::deque<uint64_t>> client_wait;  // client -> waiting arrivals
   std::vector<uint64_t> ids(n, 0);
   std::unordered_map<uint64_t, uint64_t> id_to_index;
   uint64_t next = 0, finished = 0;
+  auto admit = [&](uint64_t i, bool* busy) -> int {
+    uint64_t id = 0;
+    int rc = prng_server_submit_mode(s, items[i].client, items[i].length, items[i].form, items[i].mode, &id);
+    *busy = rc == PRNG_EBUSY;
+    if (rc) return *busy ? PRNG_OK : rc;
+    ids[i] = id;
+    id_to_index[id] = i;
+    auto& cw = client_wait[items[i].client];
+    cw.pop_front();
+    if (cw.empty()) client_wait.erase(items[i].client);
+    return PRNG_OK;
+  };
   while (finished < n) {
     const double t = s->now() - t_start;
     if (t > timeout_s) return fail(PRNG_ETIMEOUT, "trace not finished after %.1f s (%llu of %llu done)", timeout_s,
                                    (unsigned long long)finished, (unsigned long long)n);
-    while (next < n && items[next].t <= t) arrived.push_back(next++);
-    while (!arrived.empty()) {  // admission in arrival order
-      const uint64_t i = arrived.front();
-      uint64_t id = 0;
-      int rc = prng_server_submit_mode(s, items[i].client, items[i].length, items[i].form, items[i].mode, &id);
-      if (rc == PRNG_EBUSY) break;
-      if (rc) return rc;
-      ids[i] = id;
-      id_to_index[id] = i;
-      arrived.pop_front();
+    while (next < n && items[next].t <= t) {
+      arrived[lane_of(items[next].length)].push_back(next);
+      client_wait[items[next].client].push_back(next);
+      ++next;
+    }
+    for (int l = 0; l < kLanes; ++l) {
+      auto& q = arrived[l];
+      for (size_t k = 0; k < q.size();) {
+        const uint64_t i = q[k];
+        if (client_wait[items[i].client].front() != i) {  // an earlier arrival of its client waits
+          if (l > 0) break;  // longer requests stay in arrival order
+          ++k;
+          continue;
+        }
+        bool busy = false;
+        int rc = admit(i, &busy);
+        if (rc) return rc;
+        if (busy) break;
+        q.erase(q.begin() + (std::ptrdiff_t)k);
+      }
     }
     int rc = prng_server_step(s);
     if (rc) return rc;
