@@ -402,6 +402,17 @@ def extras(torch, P, g, out, stream, peak, stats_per_stream=1 << 16):
         fn()
         ms = sum(time_calls(torch, fn, reps, stream)) / reps
         res[name] = {"gsamples_s": rate(ms), "ms": ms, "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak}
+    # the bench step's fill into an output that starts 16 bytes into a 32-byte sector (a view of
+    # a larger buffer): rows then start mid-sector and take the map shifted by two outputs
+    off_buf = torch.empty(n + 4, dtype=torch.float64, device="cuda")
+    o16 = off_buf[2:2 + n]
+    fn = lambda: g.fill_mode(o16, PER_STREAM, P.FORM_B_INTBITS, P.MODE_BALANCED, None, stream)  # noqa: E731
+    fn()
+    ms = sum(time_calls(torch, fn, reps, stream)) / reps
+    res["w32_formB_balanced_at_16B_offset"] = {"gsamples_s": rate(ms), "ms": ms,
+                                               "hbm_frac": n * 8 / (ms * 1e-3) / 1e9 / peak,
+                                               "note": "output 16 bytes into a 32-byte sector"}
+    del o16, off_buf
     # a few long streams: 64 streams x 2^24 outputs (the same 2^30 outputs), cut into pieces by
     # jump-ahead so that they fill the GPU (prng_fill_split, automatic piece count)
     gl = P.Generator(SEED, 64, W)

@@ -156,10 +156,16 @@ constexpr int kNbuf = 1;  // one tile per warp: 4 blocks of 8 warps fit per SM (
 constexpr size_t kTmaSmem = (size_t)kWarpsPerBlock * kNbuf * prngd::kTileBytes + 1024;
 
 template <int W, int FORM, int MAP = 0>
-static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s) {
+static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s, bool shift) {
   const uint64_t warps = (p.n_streams + 31) / 32;
   const unsigned blocks = (unsigned)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-  if (map) {
+  if (map && shift) {
+    auto k = prngd::fill_tma_kernel<W, FORM, kNbuf, MAP, true>;
+    static std::atomic<uint64_t> attr{0};
+    const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
+    if (e != cudaSuccess) return e;
+    k<<<blocks, kWarpsPerBlock * 32, kTmaSmem, s>>>(p, *map);
+  } else if (map) {
     auto k = prngd::fill_tma_kernel<W, FORM, kNbuf, MAP>;
     static std::atomic<uint64_t> attr{0};
     const cudaError_t e = prngd::smem_limit_once(k, (int)kTmaSmem, attr);
@@ -172,10 +178,10 @@ static cudaError_t launch_w_form(const FillParams& p, const CUtensorMap* map, cu
 }
 
 template <int FORM, int MAP = 0>
-static cudaError_t launch_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s) {
-  if (p.w == 32) return launch_w_form<32, FORM, MAP>(p, map, s);
-  if (p.w == 24) return launch_w_form<24, FORM, MAP>(p, map, s);
-  return launch_w_form<0, FORM, MAP>(p, map, s);
+static cudaError_t launch_form(const FillParams& p, const CUtensorMap* map, cudaStream_t s, bool shift) {
+  if (p.w == 32) return launch_w_form<32, FORM, MAP>(p, map, s, shift);
+  if (p.w == 24) return launch_w_form<24, FORM, MAP>(p, map, s, shift);
+  return launch_w_form<0, FORM, MAP>(p, map, s, shift);
 }
 
 // Host memory the device can address (pinned / registered); its device-side address in *dev.
@@ -222,20 +228,34 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
                     (form == PRNG_FORM_B_INTBITS || form == PRNG_FORM_C_F32PAIR);
   int map_bits = map_bits_of(form, mode);
   if (!fast && form != PRNG_FORM_A_FP64) map_bits &= ~prngd::kMapCvt;  // form B's route: pair kernels only
-  if (form == PRNG_FORM_A_FP64 && map_bits == prngd::kMapCvt) {  // balanced form A under Eq. 4
-    e = launch_form<prngd::kFormA, prngd::kMapCvt>(p, mp, s);
+  const bool balanced_a = form == PRNG_FORM_A_FP64 && map_bits == prngd::kMapCvt;
+  const bool generic_map = (map_bits || form == PRNG_FORM_L_ALGO1) && !fast && !balanced_a;
+  // Rows that all start 16 bytes into a 32-byte sector: every tensor store would begin and end in
+  // half a sector. The kernels of the plain forms and of the fast maps then take a map that
+  // starts 2 outputs into each row (fill_tma_kernel's SHIFT); the generic map kernels keep theirs.
+  bool shift = false;
+  if (mp && !generic_map && ((uintptr_t)out & 31) == 16 && (per_stream & 3) == 0 && per_stream > 2) {
+    CUtensorMap smap;
+    if (encode_out_map_box(&smap, (uint64_t*)out + 2, n_streams, per_stream - 2, (uint32_t)prngd::kChunk, 32,
+                           per_stream * 8)) {
+      map = smap;
+      shift = true;
+    }
+  }
+  if (balanced_a) {  // balanced form A under Eq. 4
+    e = launch_form<prngd::kFormA, prngd::kMapCvt>(p, mp, s, shift);
     if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));
     return PRNG_OK;
   }
   if (map_bits || form == PRNG_FORM_L_ALGO1) {
-    e = fast ? launch_fill_map_fast(p, form, map_bits, mp, s) : launch_fill_map(p, form, map_bits, mp, s);
+    e = fast ? launch_fill_map_fast(p, form, map_bits, mp, s, shift) : launch_fill_map(p, form, map_bits, mp, s);
     if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));
     return PRNG_OK;
   }
   switch (form) {
-    case PRNG_FORM_A_FP64: e = launch_form<prngd::kFormA>(p, mp, s); break;
-    case PRNG_FORM_B_INTBITS: e = launch_form<prngd::kFormB>(p, mp, s); break;
-    case PRNG_FORM_C_F32PAIR: e = launch_form<prngd::kFormC>(p, mp, s); break;
+    case PRNG_FORM_A_FP64: e = launch_form<prngd::kFormA>(p, mp, s, shift); break;
+    case PRNG_FORM_B_INTBITS: e = launch_form<prngd::kFormB>(p, mp, s, shift); break;
+    case PRNG_FORM_C_F32PAIR: e = launch_form<prngd::kFormC>(p, mp, s, shift); break;
     default: return fail(PRNG_EINVAL, "unknown form %d", form);
   }
   if (e != cudaSuccess) return fail(PRNG_ECUDA, "fill launch: %s", cudaGetErrorString(e));

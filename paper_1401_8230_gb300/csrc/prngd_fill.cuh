@@ -630,7 +630,11 @@ __device__ __forceinline__ void st_shared_v2(uint32_t addr, uint64_t a, uint64_t
 // * 16)), and lane 0 issues one 2D bulk tensor store of the 32 x 16 box. Rows past n_streams
 // and columns past per_stream fall outside the tensor and are not written. NBUF tiles per
 // warp let the next chunk's staging proceed while the previous store still reads shared memory.
-template <int W, int FORM, int NBUF, int MAP = 0>
+// SHIFT: rows start 16 bytes into a 32-byte sector (every row, as per_stream is a multiple of 4),
+// and the map starts 2 outputs into each row, on a sector boundary, with the rows' own pitch:
+// each lane makes its row's first two outputs first, keeps them in registers while the rest of
+// the row goes out in whole sectors, and writes them with one 16-byte store at the end.
+template <int W, int FORM, int NBUF, int MAP = 0, bool SHIFT = false>
 __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
                                                        const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ uint8_t smem_raw[];
@@ -648,10 +652,21 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
   const uint32_t row_off = (uint32_t)lane * 128u;
   const uint32_t sw = (uint32_t)(lane & 7);
   const int y0 = (int)(warp_global * 32);
+  uint64_t head0 = 0, head1 = 0;
+  if constexpr (SHIFT) {
+    if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
+      next_pair<W, FORM, MAP>(st, rej, p, head0, head1, cvt_group_mask<FORM, W, MAP>() & 1u,
+                              (cvt_group_mask<FORM, W, MAP>() >> 1) & 1u);
+    } else {
+      head0 = next_output<W, FORM, MAP>(st, rej, p);
+      head1 = next_output<W, FORM, MAP>(st, rej, p);
+    }
+  }
+  const uint64_t span = p.per_stream - (SHIFT ? 2u : 0u);  // outputs the map covers per row
   uint32_t chunk_idx = 0;
-  for (uint64_t x0 = 0; x0 < p.per_stream; x0 += kChunk, ++chunk_idx) {
+  for (uint64_t x0 = 0; x0 < span; x0 += kChunk, ++chunk_idx) {
     uint64_t v[kChunk];
-    const uint64_t left = p.per_stream - x0;
+    const uint64_t left = span - x0;
     if (left >= (uint64_t)kChunk) {
       if constexpr ((W == 32 || W == 24) && (FORM == kFormB || FORM == kFormC)) {
 #pragma unroll
@@ -691,6 +706,7 @@ __global__ void __launch_bounds__(256, 4) fill_tma_kernel(const FillParams p,
   }
   if (lane == 0) bulk_wait_all();
   if (active) {
+    if constexpr (SHIFT) *(ulonglong2*)(p.out + stream * p.per_stream) = make_ulonglong2(head0, head1);
     p.state[stream] = make_uint4(st.x, st.y, st.z, st.w);
     if (p.rejects) p.rejects[stream] = rej;
   }

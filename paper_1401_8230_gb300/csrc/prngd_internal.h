@@ -70,7 +70,7 @@ inline int map_bits_of(int form, int mode) {
 // prngd_modes_fast.cu): `map` as map_bits_of; `tmap` is null for the plain store path.
 cudaError_t launch_fill_map(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap, cudaStream_t s);
 cudaError_t launch_fill_map_fast(const prngd::FillParams& p, int form, int map, const CUtensorMap* tmap,
-                                 cudaStream_t s);
+                                 cudaStream_t s, bool shift = false);
 int host_fill(prng_ctx* h, double* host_out, uint64_t per_stream, int form, uint64_t* host_rejects);
 bool device_mapped_host(const void* p, void** dev);
 bool encode_out_map(CUtensorMap* map, void* out, uint64_t n_streams, uint64_t per_stream);

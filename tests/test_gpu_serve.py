@@ -170,3 +170,22 @@ def test_cancel_withdraws_a_waiting_request():
             assert P.prng_server_info(srv)["completed"] == 2
         finally:
             P.prng_server_destroy(srv)
+
+
+def test_served_requests_in_every_lane_match_client_model():
+    """Requests of every length class of the server's lanes (up to 2^20 outputs, up to 2^24,
+    longer), interleaved across clients so that the lanes' batches overlap on the device; each
+    result equals the client model (its streams continued in submission order)."""
+    seed, S, n_clients, min_per, w = 13, 64, 2, 1024, 32
+    seq = []
+    for c in range(n_clients):
+        seq += [(c, 2**20 + 7, P.FORM_B_INTBITS), (c, 5000, P.FORM_A_FP64), (c, 2**24 + 5, P.FORM_C_F32PAIR),
+                (c, 300, P.FORM_B_INTBITS), (c, 2**22 + 16, P.FORM_A_FP64)]
+    order = [0, 5, 1, 6, 2, 7, 3, 8, 4, 9]  # alternate the two clients
+    seq = [seq[i] for i in order]
+    results, info = run_sequence(seed, w, S, n_clients, min_per, 1 << 30, seq, step_every=1)
+    assert info["completed"] == len(seq)
+    models = {}
+    for i, (c, L, f) in enumerate(seq):
+        m = models.setdefault(c, ClientModel(seed, c, S, min_per, w))
+        assert same(results[i], m.request(L, f)), (i, c, L, f)
