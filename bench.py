@@ -641,7 +641,7 @@ def served(torch, P, plain_rate, seconds, mix_rate=None):
     lat = np.asarray(lat)
     length = np.array([r["length"] for r in trace])  # the server's lanes by request length
     classes = (("le_2p20", length <= 2**20), ("2p20_to_2p24", (length > 2**20) & (length <= 2**24)),
-               ("gt_2p24", length > 2**24))
+               ("2p24_to_2p26", (length > 2**24) & (length <= 2**26)), ("gt_2p26", length > 2**26))
     lanes = {name: {"requests": int(m.sum()), "p50_ms": float(np.percentile(lat[m], 50) * 1e3),
                     "p99_ms": float(np.percentile(lat[m], 99) * 1e3)}
              for name, m in classes if m.any()}

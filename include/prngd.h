@@ -394,8 +394,8 @@ int prng_batch_autotune(prng_t h, int form, uint64_t length_lo, uint64_t length_
  * (allocated once by prng_server_create) and returns PRNG_EBUSY when it does not fit;
  * the caller retries after releasing finished requests.
  * Batching: prng_server_step harvests finished batches and launches the admitted requests of
- * idle clients as batches, one per lane: requests of up to 2^20 outputs, up to 2^24, and
- * longer. Up to 8 batches of a lane are on the device at once, each on a CUDA stream of its
+ * idle clients as batches, one per lane: requests of up to 2^20 outputs, up to 2^24, up to
+ * 2^26, and longer. Up to 8 batches of a lane are on the device at once, each on a CUDA stream of its
  * own (lanes of shorter requests at higher stream priority), so work admitted while other
  * batches run overlaps with them. The server's batches take one item (32 rows) per warp and
  * then end their blocks, which frees SM slots item by item for the other lanes.
