@@ -135,3 +135,18 @@ def test_few_long_streams_bulk_size():
         assert np.array_equal(states(g), split_state)
     del out, ref
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("segments", [256, 8192, 16384])
+def test_split_segment_counts_at_the_jump_kernels_bounds(segments):
+    """From 256 segments per stream on, a block's rows lie in one stream and each row is a sum of
+    shared powers T^i u (256 and 8192: one table digit; 16384: the block's high digit first
+    moves u); fewer segments (the other split tests) take the jump from the state. w = 8 puts
+    many rejects before most segments."""
+    seed, ns, per, w = 17, 3, 2**15, 8
+    (a, ra, sa), (b, rb, sb) = run_pair(seed, ns, w, per, P.FORM_B_INTBITS, 0, segments)
+    assert np.array_equal(a.view(np.uint64), b.view(np.uint64)) and np.array_equal(ra, rb)
+    assert np.array_equal(sa, sb)
+    want, wrej = O.fill(seed, 0, ns, per, w, O.FORM_B)
+    assert np.array_equal(a.view(np.uint64), want.view(np.uint64))
+    assert wrej.sum() > 500  # about 2/256 of 98304 attempts
