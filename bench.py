@@ -610,16 +610,17 @@ def batched(torch, P, stream, plain_rate, n_req=4096, hi=2**26, tune=True, rates
                               "gsamples_s": (total / (default_ms * 1e-3) / 1e9) if default_ms else None}}
 
 
-def served(torch, P, plain_rate, seconds, mix_rate=None):
+def served(torch, P, plain_rate, seconds, mix_rate=None, streams_per_client=32768):
     """Poisson arrivals at 20k requests/s for `seconds`, lengths log-uniform in [2^10, 2^28],
-    form uniform over A/B/C, 2^16 clients with 16384 resident streams each (16 GiB of state),
-    32 GiB output pool; requests replayed in real time by the library's serving loop. Then the
-    same server at saturation (all of a fixed request set arriving at once)."""
+    form uniform over A/B/C, 2^16 clients with `streams_per_client` resident streams each (16 B
+    of state a stream), 32 GiB output pool; requests replayed in real time by the library's
+    serving loop. Then the same server at saturation (all of a fixed request set arriving at
+    once)."""
     import numpy as np
 
     from paper_1401_8230_gb300 import workloads
 
-    clients, S = 2**16, 16384
+    clients, S = 2**16, streams_per_client
     g = P.Generator(SEED, clients * S, W)
     srv = P.prng_server_create(g.h, S, 1024, 32 << 30)
     try:
@@ -653,7 +654,7 @@ def served(torch, P, plain_rate, seconds, mix_rate=None):
             "plain_fill_of_form_mix_gsamples_s": mix_rate,
             "saturation_vs_plain_fill_of_form_mix": (sat_rate / mix_rate) if mix_rate else None,
             "saturation_requests": len(sat),
-            "workload": "Poisson 20k req/s, log-uniform [2^10, 2^28], forms A/B/C, 2^16 clients x 16384 streams, "
+            "workload": f"Poisson 20k req/s, log-uniform [2^10, 2^28], forms A/B/C, 2^16 clients x {S} streams, "
                         "32 GiB pool"}
 
 

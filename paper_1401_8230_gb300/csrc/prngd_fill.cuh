@@ -220,6 +220,12 @@ __device__ __forceinline__ uint32_t complement_fma(uint32_t u, uint32_t neg_one)
 // I = A 2^32 + 2A + u2 + (X >> 32) + PLUS: Eq. 4 with (K1, C0, PLUS) = (3, -1, 1), X = 2B + 3A;
 // Eq. 5 with (4, -4, 0 or 1), X = 4A + 2 u2. The check is 1 when 2^22 <= A <= 2^32 - 4 and the
 // low word of X is below LIM; I is meaningless otherwise.
+// The wide multiply-adds form K1 u1 + 2 u2 = X - C0 with no 64-bit constant, and C0 is added to
+// the low word alone, which gives X's low word exactly. Its high word is X's whenever X's low
+// word is below 2^32 + C0, which the check (LIM <= 2^32 - 64 for Eq. 5, 2^32 - 8 for Eq. 4)
+// ensures. (Measured on the bulk fill against C0 as the 64-bit addend of the first multiply-add,
+// Gsamples/s: integer-only form B 676 -> 708, balanced 732 -> 751, form C 563 -> 571, Eq. 5
+// 679 -> 707 and 733 -> 755, 1 - z 645 -> 670.)
 //
 // Both outputs of a pair (draws x, y and z, w), with one check for the two.
 template <int K1, int C0, int PLUS, unsigned LIM>
@@ -230,12 +236,14 @@ __device__ __forceinline__ uint32_t fast32_pair_I_ptx_t(uint32_t x, uint32_t y, 
       ".reg .u64 Ya, Xa, Pa, Ja, Yb, Xb, Pb, Jb;\n\t"
       ".reg .u32 xla, fa, aa, Aa, ga, ila, iha, xlb, fb, ab, Ab, gb, ilb, ihb;\n\t"
       ".reg .pred p1, p2, p3, p4;\n\t"
-      "mad.wide.u32 Ya, %4, 2, %8;\n\t"
-      "mad.wide.u32 Xa, %3, %9, Ya;\n\t"         // X of output a
+      "mul.wide.u32 Ya, %4, 2;\n\t"
+      "mad.wide.u32 Xa, %3, %9, Ya;\n\t"         // X of output a, less C0
       "mov.b64 {xla, fa}, Xa;\n\t"
-      "mad.wide.u32 Yb, %6, 2, %8;\n\t"
-      "mad.wide.u32 Xb, %5, %9, Yb;\n\t"         // X of output b
+      "mad.lo.u32 xla, xla, %7, %8;\n\t"
+      "mul.wide.u32 Yb, %6, 2;\n\t"
+      "mad.wide.u32 Xb, %5, %9, Yb;\n\t"         // X of output b, less C0
       "mov.b64 {xlb, fb}, Xb;\n\t"
+      "mad.lo.u32 xlb, xlb, %7, %8;\n\t"
       "mad.lo.u32 aa, %3, %7, -4194305;\n\t"
       "mad.lo.u32 ab, %5, %7, -4194305;\n\t"
       "setp.lt.u32 p1, aa, 0xFFBFFFFD;\n\t"      // both A in [2^22, 2^32 - 4], both low words of X
@@ -273,9 +281,10 @@ __device__ __forceinline__ uint64_t fast32_I_ptx_t(uint32_t u1, uint32_t u2, uin
       ".reg .u64 Y, X, P, Ip;\n\t"
       ".reg .u32 xlo, f, a, A, g, ilo, ihi;\n\t"
       ".reg .pred p1, p2;\n\t"
-      "mad.wide.u32 Y, %3, 2, %5;\n\t"
+      "mul.wide.u32 Y, %3, 2;\n\t"
       "mad.wide.u32 X, %2, %6, Y;\n\t"
       "mov.b64 {xlo, f}, X;\n\t"
+      "mad.lo.u32 xlo, xlo, %4, %5;\n\t"
       "mad.lo.u32 a, %2, %4, -4194305;\n\t"
       "setp.lt.u32 p1, a, 0xFFBFFFFD;\n\t"
       "setp.lt.and.u32 p2, xlo, %8, p1;\n\t"

@@ -48,6 +48,7 @@ int launch_stats(prng_ctx* h, uint64_t per_stream, uint64_t* d_hist, uint64_t* d
   p.dc = h->dc;
   p.w = h->w;
   p.unit = stats_block_size(h->n_streams, h->num_sms);
+  p.one = 1;
   cudaError_t e;
   if (h->w == 32)
     e = launch_stats_w<32>(p, h->num_sms, s);

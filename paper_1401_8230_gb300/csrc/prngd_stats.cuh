@@ -19,6 +19,7 @@ struct StatsParams {
   DivConst dc;
   int w;
   uint32_t unit;      // streams per work unit (= block size)
+  uint32_t one;       // 1, read at run time (multiply-adds by it stay on the FMA pipe)
 };
 
 constexpr int kHistWords = 32768;  // word i holds bin i (low half) and bin i + 32768 (high half)
@@ -48,11 +49,33 @@ __device__ __forceinline__ uint32_t next_t(XorShift128& st, uint32_t& rej, const
   if constexpr (W == 32) {
     // floor(V 2^64) = A 2^32 + (B + 2A) + (X >> 32) when the low word of X is not within 8 of
     // 2^32 (see fast32_bits); its high word is t.
-    const uint64_t X = fast32_X(u1, u2);
-    if (__builtin_expect((((uint32_t)(u1 - 1u) < 0xFFFFFFFEu) & ((uint32_t)X < 0xFFFFFFF8u)) != 0, 1)) {
-      const uint64_t S = (uint64_t)u1 * 2u + (uint64_t)u2 - 1u + (X >> 32);
-      return (u1 - 1u) + (uint32_t)(S >> 32);
-    }
+    // As the fill's PTX: 3 u1 + 2 u2 = X + 1 by a wide multiply and multiply-add (no 64-bit
+    // constant), X's low word by one 32-bit multiply-add, then A 2^32 + 2A + u2 + (X >> 32) + 1
+    // with the carry into the high word, which is t (measured at 2^36 outputs: 549 -> 586
+    // Gsamples/s against the same sums in C, which carried the -1 as a 64-bit constant).
+    uint32_t t, ok;
+    asm("{\n\t"
+        ".reg .u64 Y, X, P, J;\n\t"
+        ".reg .u32 xlo, f, A, g, jlo, jhi;\n\t"
+        ".reg .pred p1, p2;\n\t"
+        "mul.wide.u32 Y, %3, 2;\n\t"
+        "mad.wide.u32 X, %2, 3, Y;\n\t"
+        "mov.b64 {xlo, f}, X;\n\t"
+        "mad.lo.u32 xlo, xlo, %4, -1;\n\t"
+        "mad.lo.u32 A, %2, %4, -1;\n\t"
+        "setp.lt.u32 p1, A, 0xFFFFFFFE;\n\t"
+        "setp.lt.and.u32 p2, xlo, 0xFFFFFFF8, p1;\n\t"
+        "selp.u32 %1, 1, 0, p2;\n\t"
+        "mov.b64 P, {%3, A};\n\t"
+        "mad.wide.u32 J, A, 2, P;\n\t"
+        "mad.lo.u32 g, f, %4, 1;\n\t"
+        "mov.b64 {jlo, jhi}, J;\n\t"
+        "add.cc.u32 jlo, jlo, g;\n\t"
+        "addc.u32 %0, jhi, 0;\n\t"
+        "}"
+        : "=r"(t), "=r"(ok)
+        : "r"(u1), "r"(u2), "r"(p.one));
+    if (__builtin_expect(ok != 0, 1)) return t;
   } else if constexpr (W == 24) {
     const uint64_t K = fast24_K(u1, u2);
     if (__builtin_expect((((uint32_t)(u1 - 1u) < 0xFFFFFEu) & ((uint32_t)K < 0xFFFFFFF0u)) != 0, 1)) {
