@@ -309,3 +309,48 @@ def test_requests_16_bytes_into_a_sector(forms, chunk_depth):
         assert np.array_equal(rrej.cpu().numpy().astype(np.uint64), wr)
         assert (torch.cat([rpool[:2], rpool[2 + 64 * 96:]]).cpu().numpy() == sentinel).all()
         P.prng_batch_set_shape(g.h, 8, 3, 4, 16)
+
+
+def test_batched_workload_full_size_sampled():
+    """The batched workload at full size, as the bench runs it: 4096 fresh requests of
+    log-uniform length in [2^8, 2^26] (22.2 G outputs, 178 GB), each output on a 256-byte
+    boundary of one pool, form B's values by the balanced route, one launch per shape (the
+    default shape and a tuned one). Sampled rows (each a stream of the request's seed) of 24
+    requests and of the shortest and longest equal the oracle, and the words between a
+    request's end and the next request's start keep their sentinel."""
+    spec = workloads.batched_requests(n=4096, lo=2**8, hi=2**26, seed=1)
+    sizes = [((r["length"] + 1) // 2 * 2 + 31) // 32 * 32 for r in spec]
+    total = sum(sizes)
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < total * 8 + (8 << 30):
+        pytest.skip(f"needs {total * 8 / 2**30:.0f} GiB of device memory")
+    sentinel = -3.0
+    pool = torch.full((total,), sentinel, dtype=torch.float64, device="cuda")
+    offs, reqs, off = [], [], 0
+    for r, sz in zip(spec, sizes):
+        offs.append(off)
+        reqs.append(P.fresh_request(pool[off:], r["length"], r["seed"], r["first_stream"], P.FORM_B_INTBITS,
+                                    0, None, P.MODE_BALANCED))
+        off += sz
+    rng = np.random.default_rng(5)
+    lengths = np.array([r["length"] for r in spec])
+    pick = list(rng.choice(len(spec), 24, replace=False)) + [int(lengths.argmin()), int(lengths.argmax())]
+    try:
+        with P.Generator(1, 1, 32) as g:
+            for shape in [(8, 3, 4, 16), (4, 8, 1, 16)]:
+                P.prng_batch_set_shape(g.h, *shape)
+                P.prng_wait(g.h, P.prng_submit(g.h, reqs), 300)
+                for i in pick:
+                    r, L, chunk = spec[i], spec[i]["length"], 1024
+                    rows = (L + chunk - 1) // chunk
+                    for j in sorted({0, rows - 1, int(rng.integers(0, rows))}):
+                        cnt = min(chunk, L - j * chunk)
+                        got = pool[offs[i] + j * chunk:offs[i] + j * chunk + cnt].cpu().numpy()
+                        want, _ = O.fill(r["seed"], r["first_stream"] + j, 1, cnt, 32, O.FORM_B)
+                        assert same(got, want), (shape, i, j)
+                    pad = pool[offs[i] + L:offs[i] + sizes[i]].cpu().numpy()
+                    assert (pad == sentinel).all(), (shape, i)
+    finally:
+        del pool
+        torch.cuda.empty_cache()

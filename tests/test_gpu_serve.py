@@ -189,3 +189,38 @@ def test_served_requests_in_every_lane_match_client_model():
     for i, (c, L, f) in enumerate(seq):
         m = models.setdefault(c, ClientModel(seed, c, S, min_per, w))
         assert same(results[i], m.request(L, f)), (i, c, L, f)
+
+
+def test_served_full_size_sampled_streams_match_client_model():
+    """The serving configuration the bench runs: 2^16 clients x 32768 resident streams (2^31
+    streams, 32 GiB of state), a 32 GiB output pool, rows from 1024 outputs. Requests of every
+    lane, among them a 2^28-output one (rows of 8192 on all 32768 streams of its client), run
+    interleaved across three clients; for each client a fixed set of streams (first, second,
+    middle, last, random) is followed through the oracle across all of that client's requests,
+    and every row of those streams equals the served result."""
+    seed, S, n_clients, min_per, w = 1, 32768, 2**16, 1024, 32
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < (80 << 30):
+        pytest.skip("needs 80 GiB of device memory")
+    seq = [(7, 2**28 - 3, P.FORM_B_INTBITS), (65535, 2**24 + 1, P.FORM_B_INTBITS), (0, 300, P.FORM_B_INTBITS),
+           (7, 5000, P.FORM_A_FP64), (65535, 2**20, P.FORM_A_FP64), (7, 2**26 + 17, P.FORM_C_F32PAIR),
+           (0, 2**25 + 2, P.FORM_C_F32PAIR)]
+    results, info = run_sequence(seed, w, S, n_clients, min_per, 32 << 30, seq, step_every=1)
+    assert info["completed"] == len(seq)
+    rng = np.random.default_rng(3)
+    track = {c: sorted({0, 1, S // 2, S - 1, int(rng.integers(0, S))}) for c, _, _ in seq}
+    states = {(c, j): O.stream_seed(seed, c * S + j) for c in track for j in track[c]}
+    compared = 0
+    for i, (c, L, f) in enumerate(seq):  # each client's requests in submission order
+        n = min(S, -(-L // min_per))
+        per = 16 * -(-L // (16 * n))
+        for j in track[c]:
+            cnt = max(0, min(per, L - j * per)) if j < n else 0
+            if cnt == 0:
+                continue
+            v, _, states[(c, j)] = O.fill_state(states[(c, j)], cnt, w, OF[f])
+            k = 2 if f == P.FORM_C_F32PAIR else 1  # form C: two floats an output
+            assert same(results[i][k * j * per:k * (j * per + cnt)], v), (i, c, j)
+            compared += 1
+    assert compared >= 20
