@@ -68,11 +68,14 @@ __global__ void jump_rows_kernel(const uint4* __restrict__ base, uint4* __restri
 // share the high base-8192 digit k1 of their segment index j = k0 + 8192 k1. With
 // u = T^(delta 8192 k1) s, T^(delta j) s = T^(delta k0) u = sum_i g_i T^i u with
 // g = x^(delta k0) mod P, and the 128 states T^i u are the same for every row of the block:
-// one thread makes u (a jump from the state) and steps the powers into shared memory, and each
-// row is then 128 masked xors of them, with no generator steps (a jump from the state alone
-// also steps the generator 128 times). Measured on the 2^20 rows of 64 streams x 16384 segments:
-// 117 us from the state, 57 us from shared powers, where the masked xors load the ALU pipe;
-// making the powers once per group in a separate kernel saved no more (55 us).
+// one thread makes u (a jump from the state) and steps the powers into shared memory, the
+// block tabulates the xor of every subset of each 4 consecutive powers, and each row is then 32
+// table entries (one per 4 coefficients of g) xored together, with no generator steps (a jump
+// from the state alone also steps the generator 128 times). Measured on the 2^20 rows of 64
+// streams x 16384 segments: 117 us from the state, 57 us from shared powers by 128 masked xors
+// (the ALU pipe's load), about 14 us less with the 4-coefficient table (the split call 639 ->
+// 644 Gsamples/s in one harness); making the powers once per group in a separate kernel saved
+// no more than the masked xors did (55 us).
 // u = T^(delta 8192 k1) s: the block's high digit, once per block, out of line so that its
 // registers do not count against the row loop's occupancy.
 __device__ __noinline__ XorShift128 jump_high_digit(const uint4* __restrict__ table, uint32_t k1, XorShift128 st) {
@@ -100,6 +103,25 @@ __global__ void __launch_bounds__(256) jump_rows_shared_kernel(const uint4* __re
     }
   }
   __syncthreads();
+  // The xor of every subset of each four consecutive powers (32 groups x 16 subsets), so that a
+  // row takes one table entry per 4 coefficients: 32 loads and xors instead of 128 masked ones.
+  __shared__ uint4 combo[32 * 16];
+  for (uint32_t e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
+    const uint32_t grp = e >> 4, c = e & 15u;
+    uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if ((c >> b) & 1u) {
+        const uint4 v = powers[4 * grp + b];
+        acc.x ^= v.x;
+        acc.y ^= v.y;
+        acc.z ^= v.z;
+        acc.w ^= v.w;
+      }
+    }
+    combo[e] = acc;
+  }
+  __syncthreads();
   const uint64_t row = row0 + threadIdx.x;
   if (row >= n_rows) return;
   const uint32_t j = (uint32_t)(row & seg_mask);
@@ -115,13 +137,12 @@ __global__ void __launch_bounds__(256) jump_rows_shared_kernel(const uint4* __re
 #pragma unroll
   for (int word = 0; word < 4; ++word) {
 #pragma unroll
-    for (int b = 0; b < 32; ++b) {
-      const uint32_t m = 0u - ((g[word] >> b) & 1u);  // all ones when the coefficient is set
-      const uint4 v = powers[32 * word + b];
-      ax ^= v.x & m;
-      ay ^= v.y & m;
-      az ^= v.z & m;
-      aw ^= v.w & m;
+    for (int nib = 0; nib < 8; ++nib) {
+      const uint4 v = combo[16 * (8 * word + nib) + ((g[word] >> (4 * nib)) & 15u)];
+      ax ^= v.x;
+      ay ^= v.y;
+      az ^= v.z;
+      aw ^= v.w;
     }
   }
   rows[row] = make_uint4(ax, ay, az, aw);
