@@ -162,18 +162,23 @@ def test_full_size_bulk_fill_sampled(w):
         assert 64 < total_rej < 256
 
 
-def rounding_carry_rows(seed, n_streams, per):
+def rounding_carry_rows(seed, n_streams, per, w=32):
     """(stream, index) of outputs whose fast-path rounding add 2^s carries out of I's low word
     (I = floor(V 2^64), s = the rounding bit's position: ilo + 2^s >= 2^32), found from the
     oracle's raw draws with numpy (pair rule; the first 2 per draws of each stream)."""
     hits = []
     for s in range(n_streams):
         r = O.stream_raw(seed, s, 2 * per).astype(np.uint64)
-        u1, u2 = r[0::2], r[1::2]
-        ok = (u1 > np.uint64(1 << 22)) & (u1 < np.uint64(0xFFFFFFFF))  # accepted, A >= 2^22
-        A = u1 - np.uint64(1)
-        X = np.uint64(3) * u1 + np.uint64(2) * u2 - np.uint64(1)
-        I = (A << np.uint64(32)) + np.uint64(2) * A + u2 + np.uint64(1) + (X >> np.uint64(32))
+        u1, u2 = r[0::2] >> np.uint64(32 - w), r[1::2] >> np.uint64(32 - w)
+        A, B = u1 - np.uint64(1), u2 + np.uint64(1)
+        if w == 32:
+            ok = (u1 > np.uint64(1 << 22)) & (u1 < np.uint64(0xFFFFFFFF))  # accepted, A >= 2^22
+            X = np.uint64(3) * A + np.uint64(2) * B
+            I = (A << np.uint64(32)) + np.uint64(2) * A + B + (X >> np.uint64(32))
+        else:  # w = 24: I = A 2^40 + (2A + B) 2^16 + (K >> 32)
+            ok = (A >= np.uint64(1 << 14)) & (u1 < np.uint64((1 << 24) - 1))
+            K = ((np.uint64(3) * A + np.uint64(2) * B) << np.uint64(24)) + np.uint64(4) * A + np.uint64(3) * B
+            I = (A << np.uint64(40)) + ((np.uint64(2) * A + B) << np.uint64(16)) + (K >> np.uint64(32))
         ihi = (I >> np.uint64(32)).astype(np.float64)
         q = np.frexp(np.maximum(ihi, 1.0))[1] - 1  # top bit of the high word (exact below 2^53)
         step = np.left_shift(np.uint64(1), (q - 21).clip(0, 40).astype(np.uint64))
@@ -183,22 +188,22 @@ def rounding_carry_rows(seed, n_streams, per):
     return hits
 
 
-@pytest.mark.parametrize("mode", [0, P.MODE_BALANCED])
-def test_outputs_whose_rounding_carries_into_the_high_word(mode):
+@pytest.mark.parametrize("w,mode", [(32, 0), (32, P.MODE_BALANCED), (24, 0)])
+def test_outputs_whose_rounding_carries_into_the_high_word(w, mode):
     """Outputs where adding the rounding bit carries out of I's low word (probability about
     2^-23 an output): streams holding them, found on the CPU, filled on the GPU by the integer
     route (mode 0: every output; balanced: outputs 0 mod 4) and compared whole with the oracle."""
     seed, ns, per = 1, 2**15, 1024
-    hits = rounding_carry_rows(seed, ns, per)
+    hits = rounding_carry_rows(seed, ns, per, w)
     if mode:
         hits = [h for h in hits if h[1] % 4 == 0]
     assert hits, "the search must find outputs on the integer route whose rounding carries"
     streams = sorted({s for s, _ in hits})
-    with P.Generator(seed, ns, 32) as g:
+    with P.Generator(seed, ns, w) as g:
         out = torch.empty(ns * per, dtype=torch.float64, device="cuda")
         g.fill_mode(out, per, P.FORM_B_INTBITS, mode)
         torch.cuda.synchronize()
         got = out.view(ns, per)[streams].cpu().numpy()
     for k, s in enumerate(streams):
-        want, _ = O.fill(seed, s, 1, per, 32, O.FORM_B)
+        want, _ = O.fill(seed, s, 1, per, w, O.FORM_B)
         assert np.array_equal(got[k].view(np.uint64), want.view(np.uint64)), s
