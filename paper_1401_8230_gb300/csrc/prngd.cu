@@ -218,6 +218,8 @@ int launch_fill(prng_ctx* h, uint4* state, uint64_t n_streams, void* out, uint64
   p.scale = h->scale;
   p.w = h->w;
   p.one = 1;
+  // rows that do not all start on a 128-byte line: the tensor stores keep their lines in L2
+  p.keep_lines = (((uintptr_t)out & 127) != 0 || ((per_stream * 8) & 127) != 0) ? 1u : 0u;
   set_mode_constants(p, h->w, mode);
   CUtensorMap map;
   const CUtensorMap* mp = (allow_tma && encode_out_map(&map, out, n_streams, per_stream)) ? &map : nullptr;
