@@ -72,11 +72,13 @@ def test_parity_other_w_ragged(w, form):
         assert rej.sum() > 0
 
 
-@pytest.mark.parametrize("per", [1, 2, 15, 16, 17, 33, 255])
-@pytest.mark.parametrize("offset", [0, 8])
+@pytest.mark.parametrize("per", [1, 2, 15, 16, 17, 33, 255, 1024])
+@pytest.mark.parametrize("offset", [0, 8, 32, 64, 96])
 def test_store_paths_and_edges(per, offset):
     """Odd per_stream and an 8-byte (not 16-byte) aligned output take the plain store path;
-    the rest take the TMA path. Both must give the same stream-major values."""
+    the rest take the TMA path, whose stores keep their L2 lines when rows do not start on
+    128-byte lines (offsets 32, 64, 96; rows not a multiple of 16 outputs). Every path must
+    give the same stream-major values."""
     seed, w, ns = 77, 32, 33
     with P.Generator(seed, ns, w) as g:
         got, rej = gpu_fill(g, per, O.FORM_B, offset_bytes=offset)
